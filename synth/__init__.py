@@ -1,0 +1,271 @@
+"""Seeded synthetic inputs shared by the oracle tests, the GPU tests and the bench.
+
+This module holds no ARG-CSR arithmetic: it only draws CSR matrices and
+vectors.  Every generator is deterministic for a given seed (numpy PCG64).
+
+Matrix families stand in for the sparse-matrix collections the paper tests
+on (Section 5: ~1 600 square matrices from circuit, structural, finite
+difference and optimisation problems), which are not available here:
+
+* ``laplacian_2d`` / ``laplacian_3d`` -- Dirichlet 5-/7-point stencils
+  (finite-difference matrices, e.g. the paper's t2d_q, norris/torso2 family).
+* ``lognormal_rows`` -- uneven row lengths with uniformly scattered columns
+  (circuit-simulation matrices such as rajat23 / IBM_EDA have this shape).
+* ``banded`` / ``block_diag`` -- banded and block-structured matrices.
+* ``random_csr`` -- small matrices with empty rows, huge rows and
+  rectangular shapes for property tests.
+* ``fig3_example`` -- the 8-row worked example of Section 3 (Fig. 3 text).
+
+All CSR arrays are numpy: ``rowPointers`` int32[n+1], ``columns`` int32[nnz]
+(sorted within each row unless stated), ``values`` float64[nnz].
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "Csr", "laplacian_2d", "laplacian_3d", "lognormal_rows", "zipf_rows",
+    "banded", "block_diag", "random_csr", "fig3_example", "uniform_vector",
+    "pathological_overflow_rowpointers", "workload",
+]
+
+
+class Csr:
+    """A CSR matrix held as three numpy arrays (Section 2, CSR format)."""
+
+    __slots__ = ("n_rows", "n_cols", "rowPointers", "columns", "values", "name")
+
+    def __init__(self, n_rows, n_cols, rowPointers, columns, values, name=""):
+        self.n_rows = int(n_rows)
+        self.n_cols = int(n_cols)
+        self.rowPointers = np.ascontiguousarray(rowPointers, dtype=np.int32)
+        self.columns = np.ascontiguousarray(columns, dtype=np.int32)
+        self.values = np.ascontiguousarray(values)
+        self.name = name
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowPointers[-1]) if self.n_rows > 0 else 0
+
+    def row_lengths(self) -> np.ndarray:
+        return np.diff(self.rowPointers.astype(np.int64))
+
+    def astype(self, dtype) -> "Csr":
+        return Csr(self.n_rows, self.n_cols, self.rowPointers, self.columns,
+                   self.values.astype(dtype), self.name)
+
+    def to_dense(self) -> np.ndarray:
+        d = np.zeros((self.n_rows, self.n_cols), dtype=np.float64)
+        rows = np.repeat(np.arange(self.n_rows), self.row_lengths())
+        np.add.at(d, (rows, self.columns.astype(np.int64)), self.values.astype(np.float64))
+        return d
+
+    def __repr__(self):
+        return f"Csr({self.name!r}, n_rows={self.n_rows}, n_cols={self.n_cols}, nnz={self.nnz})"
+
+
+def _from_lengths(n_rows, n_cols, lengths, columns, values, name):
+    rp = np.zeros(n_rows + 1, dtype=np.int64)
+    np.cumsum(lengths, out=rp[1:])
+    if rp[-1] > np.iinfo(np.int32).max:
+        raise ValueError("nnz does not fit int32 row pointers")
+    return Csr(n_rows, n_cols, rp.astype(np.int32), columns, values, name)
+
+
+def _stencil(dims, diag):
+    """Dirichlet Laplacian on a tensor grid: diag on the diagonal, -1 to each
+    in-grid axis neighbour, columns sorted ascending within each row."""
+    dims = tuple(int(d) for d in dims)
+    n = int(np.prod(dims))
+    idx = np.arange(n, dtype=np.int64)
+    coords = np.unravel_index(idx, dims)  # C order: last axis fastest
+    strides = [int(np.prod(dims[k + 1:])) for k in range(len(dims))]
+    # candidate neighbour offsets in ascending column order
+    offs = sorted([-s for s in strides] + [0] + [s for s in strides])
+    cols = np.empty((n, len(offs)), dtype=np.int64)
+    vals = np.empty((n, len(offs)), dtype=np.float64)
+    valid = np.ones((n, len(offs)), dtype=bool)
+    for j, off in enumerate(offs):
+        cols[:, j] = idx + off
+        vals[:, j] = diag if off == 0 else -1.0
+        if off != 0:
+            k = strides.index(abs(off))
+            c = coords[k] + (1 if off > 0 else -1)
+            valid[:, j] = (c >= 0) & (c < dims[k])
+    lengths = valid.sum(axis=1)
+    return n, cols[valid], vals[valid], lengths
+
+
+def laplacian_2d(nx: int, ny: int | None = None) -> Csr:
+    """5-point Dirichlet Laplacian on an nx-by-ny grid: 4 on the diagonal,
+    -1 for each in-grid neighbour."""
+    ny = nx if ny is None else ny
+    n, c, v, l = _stencil((ny, nx), 4.0)
+    return _from_lengths(n, n, l, c, v, f"laplacian2d_{nx}x{ny}")
+
+
+def laplacian_3d(nx: int, ny: int | None = None, nz: int | None = None) -> Csr:
+    """7-point Dirichlet Laplacian on an nx-by-ny-by-nz grid: 6 on the
+    diagonal, -1 for each in-grid neighbour (symmetric positive definite)."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    n, c, v, l = _stencil((nz, ny, nx), 6.0)
+    return _from_lengths(n, n, l, c, v, f"laplacian3d_{nx}x{ny}x{nz}")
+
+
+def _distinct_sorted_columns(rng, lengths, n_cols):
+    """Per row, ``lengths[r]`` distinct columns drawn uniformly from
+    [0, n_cols), sorted ascending.  Duplicates are redrawn until none remain."""
+    lengths = np.asarray(lengths, dtype=np.int64)
+    n = lengths.size
+    nnz = int(lengths.sum())
+    if nnz == 0:
+        return np.zeros(0, dtype=np.int32)
+    if n * n_cols <= 4_000_000 or lengths.max() * 4 > n_cols:
+        # small or dense rows: exact sampling without replacement per row
+        out = np.empty(nnz, dtype=np.int64)
+        p = 0
+        for r in range(n):
+            k = int(lengths[r])
+            if k:
+                out[p:p + k] = np.sort(rng.choice(n_cols, size=k, replace=False))
+                p += k
+        return out.astype(np.int32)
+    row_of = np.repeat(np.arange(n, dtype=np.int64), lengths)
+    cols = rng.integers(0, n_cols, size=nnz, dtype=np.int64)
+    while True:
+        key = row_of * n_cols + cols
+        order = np.argsort(key, kind="stable")
+        key = key[order]
+        cols = cols[order]
+        dup = np.flatnonzero(key[1:] == key[:-1]) + 1
+        if dup.size == 0:
+            return cols.astype(np.int32)
+        cols[dup] = rng.integers(0, n_cols, size=dup.size, dtype=np.int64)
+
+
+def lognormal_rows(n: int, mu: float = 2.3, sigma: float = 1.2, max_len: int = 20000,
+                   n_cols: int | None = None, seed_structure: int = 0,
+                   seed_values: int = 1, dtype=np.float64) -> Csr:
+    """Uneven rows: length = clip(rint(lognormal(mu, sigma)), 1, max_len),
+    columns uniform without replacement over [0, n_cols), values N(0, 1)."""
+    n_cols = n if n_cols is None else n_cols
+    rs = np.random.default_rng(seed_structure)
+    lengths = np.clip(np.rint(rs.lognormal(mu, sigma, n)), 1, min(max_len, n_cols)).astype(np.int64)
+    cols = _distinct_sorted_columns(rs, lengths, n_cols)
+    vals = np.random.default_rng(seed_values).standard_normal(int(lengths.sum())).astype(dtype)
+    return _from_lengths(n, n_cols, lengths, cols, vals, f"lognormal_{n}_mu{mu}_s{sigma}")
+
+
+def zipf_rows(n: int, s: float = 1.5, max_len: int = 50000, n_cols: int | None = None,
+              seed_structure: int = 0, seed_values: int = 1, dtype=np.float64) -> Csr:
+    """Power-law rows: length = min(Zipf(s), max_len), uniform columns."""
+    n_cols = n if n_cols is None else n_cols
+    rs = np.random.default_rng(seed_structure)
+    lengths = np.minimum(rs.zipf(s, n), min(max_len, n_cols)).astype(np.int64)
+    cols = _distinct_sorted_columns(rs, lengths, n_cols)
+    vals = np.random.default_rng(seed_values).standard_normal(int(lengths.sum())).astype(dtype)
+    return _from_lengths(n, n_cols, lengths, cols, vals, f"zipf_{n}_s{s}")
+
+
+def banded(n: int, half_bandwidth: int, seed_values: int = 1, dtype=np.float64) -> Csr:
+    """Full band |i - j| <= half_bandwidth, values N(0, 1)."""
+    i = np.arange(n, dtype=np.int64)
+    lo = np.maximum(i - half_bandwidth, 0)
+    hi = np.minimum(i + half_bandwidth, n - 1)
+    lengths = hi - lo + 1
+    rows = np.repeat(i, lengths)
+    starts = np.repeat(lo, lengths)
+    rp = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(lengths, out=rp[1:])
+    cols = starts + (np.arange(rp[-1]) - np.repeat(rp[:-1], lengths))
+    del rows
+    vals = np.random.default_rng(seed_values).standard_normal(int(rp[-1])).astype(dtype)
+    return _from_lengths(n, n, lengths, cols, vals, f"banded_{n}_hb{half_bandwidth}")
+
+
+def block_diag(n_blocks: int, block: int, seed_values: int = 1, dtype=np.float64) -> Csr:
+    """Dense block x block blocks on the diagonal."""
+    n = n_blocks * block
+    i = np.arange(n, dtype=np.int64)
+    lengths = np.full(n, block, dtype=np.int64)
+    base = (i // block) * block
+    cols = (np.repeat(base, block) + np.tile(np.arange(block), n)).astype(np.int64)
+    vals = np.random.default_rng(seed_values).standard_normal(n * block).astype(dtype)
+    return _from_lengths(n, n, lengths, cols, vals, f"blockdiag_{n_blocks}x{block}")
+
+
+def random_csr(n_rows: int, n_cols: int, seed: int, mean_len: float = 4.0,
+               p_empty: float = 0.1, n_huge: int = 0, huge_len: int | None = None,
+               dtype=np.float64) -> Csr:
+    """Small irregular matrices for property tests: geometric row lengths with
+    mean ``mean_len``, a fraction ``p_empty`` of empty rows and ``n_huge`` rows
+    of length ``huge_len`` (default: n_cols) at random positions."""
+    rng = np.random.default_rng(seed)
+    if n_rows == 0:
+        return Csr(0, n_cols, np.zeros(1, np.int32), np.zeros(0, np.int32),
+                   np.zeros(0, dtype), f"random_{n_rows}x{n_cols}_s{seed}")
+    lengths = rng.geometric(1.0 / (1.0 + mean_len), n_rows) - 1
+    lengths[rng.random(n_rows) < p_empty] = 0
+    if n_huge:
+        hl = n_cols if huge_len is None else huge_len
+        lengths[rng.choice(n_rows, size=min(n_huge, n_rows), replace=False)] = hl
+    lengths = np.minimum(lengths, n_cols).astype(np.int64)
+    cols = _distinct_sorted_columns(rng, lengths, n_cols)
+    vals = rng.standard_normal(int(lengths.sum())).astype(dtype)
+    return _from_lengths(n_rows, n_cols, lengths, cols, vals, f"random_{n_rows}x{n_cols}_s{seed}")
+
+
+def fig3_example(dtype=np.float64) -> Csr:
+    """The worked example of Section 3 (Fig. 3 text): an 8x8 matrix whose
+    rows 0-6 hold one nonzero each and whose last row is full.  The figure
+    itself is not available, so the single nonzero of rows 0-6 is placed on
+    the diagonal and the values are 1..15 in storage order."""
+    lengths = np.array([1] * 7 + [8], dtype=np.int64)
+    cols = np.array(list(range(7)) + list(range(8)), dtype=np.int64)
+    vals = np.arange(1, 16, dtype=np.float64).astype(dtype)
+    return _from_lengths(8, 8, lengths, cols, vals, "fig3_example")
+
+
+def uniform_vector(n: int, seed: int, dtype=np.float64) -> np.ndarray:
+    """x ~ U[-1, 1]."""
+    return np.random.default_rng(seed).uniform(-1.0, 1.0, n).astype(dtype)
+
+
+def pathological_overflow_rowpointers(group_size: int = 128) -> tuple[np.ndarray, int]:
+    """Row pointers of a matrix whose ARG-CSR slot count exceeds 2^31 - 1.
+
+    ``group_size - 1`` rows of length 1 followed by one row of length
+    L = 2^31 // group_size + 1: with desiredChunkSize D chosen so that the
+    whole matrix forms one group of ``group_size`` rows, no thread is spare,
+    so chunkSize = L and the group needs group_size * L > 2^31 - 1 slots.
+    Returns (rowPointers, D).  Only the row pointers are materialised."""
+    G = group_size
+    L = (2 ** 31) // G + 1
+    lengths = np.array([1] * (G - 1) + [L], dtype=np.int64)
+    rp = np.zeros(G + 1, dtype=np.int64)
+    np.cumsum(lengths, out=rp[1:])
+    D = -(-int(rp[-1]) // G)  # D*G >= nnz: the group never closes on nnz
+    return rp.astype(np.int32), D
+
+
+# ---------------------------------------------------------------------------
+# Named workloads (sizes as stated in the workload descriptions)
+# ---------------------------------------------------------------------------
+
+def workload(name: str) -> tuple[Csr, np.ndarray]:
+    """Return (A, x) for a named workload.
+
+    * ``laplace2d_64``: 5-point Laplacian on 64x64 (n = 4096, nnz = 20224),
+      x ~ U[-1, 1] from seed 0.
+    * ``lognormal_2m``: n = 2 000 000, lognormal(2.3, 1.2) row lengths clipped
+      to [1, 20000], structure seed 0, values seed 1, x seed 2.
+    * ``laplace3d_128``: 7-point Laplacian on 128^3 (n = 2 097 152), x seed 2.
+    """
+    if name == "laplace2d_64":
+        return laplacian_2d(64), uniform_vector(64 * 64, 0)
+    if name == "lognormal_2m":
+        return lognormal_rows(2_000_000), uniform_vector(2_000_000, 2)
+    if name == "laplace3d_128":
+        return laplacian_3d(128), uniform_vector(128 ** 3, 2)
+    raise KeyError(name)

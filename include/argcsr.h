@@ -1,0 +1,217 @@
+/*
+ * argcsr.h -- C ABI of the GB300 (sm_103a) Adaptive Row-grouped CSR library.
+ *
+ * The library implements the method of Heller & Oberhuber, "Adaptive
+ * Row-grouped CSR format for storing of sparse matrices on GPU": conversion
+ * of a CSR matrix (Section 2) into the ARG-CSR format (Section 3) and the
+ * sparse matrix-vector product y = A x on it (Section 4).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Pointers named d_* are device pointers on the current CUDA device,
+ *    owned by the caller and borrowed for the duration of the call (or, for
+ *    asynchronous calls, until the given stream has passed the call).
+ *    Pointers named h_* are host pointers.
+ *  - argcsr_stream_t is a CUDA stream handle (it has the same type as
+ *    cudaStream_t); NULL means the legacy default stream.  Kernels are
+ *    launched on that stream, in stream order.
+ *  - Index arrays are int32; the slot offsets of the format are int32 as in
+ *    the paper's group descriptor (Listing 1), so a matrix may hold at most
+ *    2^31 - 1 slots (ARGCSR_EOVERFLOW otherwise).
+ *  - Every call returns a status; nothing aborts the process.  After
+ *    ARGCSR_ECUDA, argcsr_last_error_message() describes the CUDA error.
+ *  - There is no CPU fallback: every computation runs in this library's
+ *    CUDA kernels.
+ */
+#ifndef ARGCSR_H
+#define ARGCSR_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ARGCSR_API __attribute__((visibility("default")))
+#else
+#define ARGCSR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ARGCSR_OK        = 0,
+    ARGCSR_EINVAL    = -1,  /* an argument or the CSR input is malformed  */
+    ARGCSR_ENOMEM    = -2,  /* device allocation failed                   */
+    ARGCSR_ECUDA     = -3,  /* a CUDA runtime call or launch failed       */
+    ARGCSR_EOVERFLOW = -4,  /* more than 2^31 - 1 slots would be needed   */
+    ARGCSR_ENOTSUP   = -5   /* valid request this build does not support  */
+} argcsr_status;
+
+/* Element type of the stored values and of x and y. */
+typedef enum {
+    ARGCSR_F64  = 0,  /* values f64; x, y f64; f64 arithmetic                 */
+    ARGCSR_F32  = 1,  /* values f32; x, y f32; f32 arithmetic                 */
+    ARGCSR_BF16 = 2   /* values bf16; x, y f32; f32 arithmetic (bf16 storage) */
+} argcsr_dtype;
+
+typedef struct CUstream_st *argcsr_stream_t;
+typedef struct argcsr_matrix *argcsr_t;
+
+/* Conversion parameters (Section 3).
+ *   group_size          G, the number of chunks per group; the paper's
+ *                       blockDim.x.  32, 64 or 128.
+ *   desired_chunk_size  D >= 1, the paper's desiredChunkSize: a group is
+ *                       closed once its nonzeros exceed D * G.
+ *   vec_width           V in {1, 2, 4}.  1 is the paper's layout (element j
+ *                       of chunk c at offset + j*G + c).  V > 1 rounds the
+ *                       chunk size up to a multiple of V and stores element j
+ *                       of chunk c at offset + (j/V)*G*V + c*V + j%V, so a
+ *                       thread reads V consecutive elements at once. */
+typedef struct {
+    int32_t group_size;
+    int32_t desired_chunk_size;
+    int32_t vec_width;
+} argcsr_params;
+
+/* Sizes of a converted matrix. */
+typedef struct {
+    int32_t n_rows;
+    int32_t n_cols;
+    int64_t nnz;
+    int64_t n_groups;          /* number of argcsrGroupInfo records          */
+    int64_t n_slots;           /* S = sum over groups of chunkSize * G       */
+    int32_t group_size;
+    int32_t desired_chunk_size;
+    int32_t vec_width;
+    int32_t dtype;             /* argcsr_dtype                               */
+    int64_t spmv_bytes;        /* algorithmic bytes of one SpMV: nnz*(value
+                                  + 4) + n_cols*x + n_rows*y + 4*n_rows
+                                  + 16*n_groups (padding not counted)        */
+    int64_t device_bytes;      /* device memory the handle holds             */
+} argcsr_info_t;
+
+/* ---------------------------------------------------------------------------
+ * argcsr_create_from_csr -- CSR -> ARG-CSR conversion (Section 3).
+ *
+ * Input: a CSR matrix (Section 2) of n_rows x n_cols with nnz entries:
+ *   d_rowPointers int32[n_rows + 1], d_columns int32[nnz],
+ *   d_values      nnz elements of `dtype` (f64, f32 or bf16).
+ * The CSR arrays are validated on the device (rowPointers[0] == 0,
+ * non-decreasing, rowPointers[n_rows] == nnz, 0 <= columns < n_cols): a
+ * malformed input returns ARGCSR_EINVAL and no handle.  Explicit zeros and
+ * repeated columns are kept as entries.
+ *
+ * Steps, all in device kernels on `stream`: grouping of rows (a group is
+ * closed after the row that takes its nonzero count above D*G, or before a
+ * row would become its (G+1)-th row); per group the chunk size of the greedy
+ * thread assignment (the smallest C with sum over rows of max(1, ceil(len/C))
+ * <= G, rounded up to a multiple of V); per row the group-local inclusive
+ * prefix of its thread count (threadsMapping); group offsets; the chunk-wise
+ * copy into the interleaved values/columns arrays, padded with column -1 and
+ * value +0.0.
+ *
+ * The call synchronises `stream` twice (to size the output and to return the
+ * validation status) and returns only when the handle is complete.  The
+ * handle owns its device arrays (allocated from a stream-ordered pool owned
+ * by this library) until argcsr_destroy.  *out is set to NULL on error.
+ * ------------------------------------------------------------------------ */
+ARGCSR_API argcsr_status argcsr_create_from_csr(
+    int32_t n_rows, int32_t n_cols, int64_t nnz,
+    const int32_t *d_rowPointers, const int32_t *d_columns, const void *d_values,
+    argcsr_dtype dtype, const argcsr_params *params,
+    argcsr_stream_t stream, argcsr_t *out);
+
+/* ---------------------------------------------------------------------------
+ * argcsr_spmv -- y = A x on ARG-CSR (Section 4).
+ *
+ * d_x: n_cols elements, d_y: n_rows elements, both f64 for ARGCSR_F64 and
+ * f32 otherwise.  x and y must not overlap (ARGCSR_EINVAL).  Every row of y
+ * is written, empty rows with 0.  Asynchronous on `stream`; one kernel.
+ * For f64 the result equals the CSR sum up to summation order: each chunk
+ * is summed in element order with fused multiply-adds, then the partial sums
+ * of a row's chunks are added.
+ * ------------------------------------------------------------------------ */
+ARGCSR_API argcsr_status argcsr_spmv(argcsr_t A, const void *d_x, void *d_y,
+                                     argcsr_stream_t stream);
+
+/* Sizes and byte counts of a handle (host only, no device work). */
+ARGCSR_API argcsr_status argcsr_info(argcsr_t A, argcsr_info_t *out);
+
+/* ---------------------------------------------------------------------------
+ * argcsr_export -- copy the format's arrays to host memory (synchronous on
+ * the legacy default stream after a device synchronisation).
+ *   h_groupInfo       int32[4 * n_groups]: {firstRow, size, offset, chunkSize}
+ *                     per group (Listing 1);
+ *   h_threadsMapping  int32[n_rows];
+ *   h_columns         int32[n_slots];
+ *   h_values          n_slots elements of the handle's dtype.
+ * Any pointer may be NULL to skip that array.
+ * ------------------------------------------------------------------------ */
+ARGCSR_API argcsr_status argcsr_export(argcsr_t A, int32_t *h_groupInfo,
+                                       int32_t *h_threadsMapping, int32_t *h_columns,
+                                       void *h_values);
+
+/* Borrow the handle's device arrays (valid until argcsr_destroy).  Any
+ * output pointer may be NULL. */
+ARGCSR_API argcsr_status argcsr_device_arrays(argcsr_t A, const int32_t **d_groupInfo,
+                                              const int32_t **d_threadsMapping,
+                                              const int32_t **d_columns,
+                                              const void **d_values);
+
+/* Free the handle's arrays in stream order on `stream` and the handle
+ * itself.  NULL-safe.  Work already queued on other streams that reads the
+ * handle must be ordered before `stream` by the caller. */
+ARGCSR_API argcsr_status argcsr_destroy(argcsr_t A, argcsr_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Baseline: SpMV straight on CSR (Section 2), for comparison only.
+ *   variant 0: one thread per row (scalar CSR);
+ *   variant 1: a group of 2..32 lanes per row, sized from the mean row
+ *              length (vector CSR).
+ * Arrays as in argcsr_create_from_csr; x, y as in argcsr_spmv.  No
+ * validation of the CSR content beyond the argument checks.
+ * ------------------------------------------------------------------------ */
+ARGCSR_API argcsr_status argcsr_baseline_csr_spmv(
+    int32_t n_rows, int32_t n_cols, int64_t nnz,
+    const int32_t *d_rowPointers, const int32_t *d_columns, const void *d_values,
+    argcsr_dtype dtype, int32_t variant, const void *d_x, void *d_y,
+    argcsr_stream_t stream);
+
+/* Miscellaneous ------------------------------------------------------------ */
+
+/* Human-readable name of a status code (static storage). */
+ARGCSR_API const char *argcsr_status_string(argcsr_status status);
+
+/* Text of the last CUDA error this library saw in the calling thread
+ * (static thread-local storage; empty if none). */
+ARGCSR_API const char *argcsr_last_error_message(void);
+
+/* Number of kernels this library has launched in this process. */
+ARGCSR_API uint64_t argcsr_launch_count(void);
+
+/* Return the cached, currently unused memory of the library's pool on the
+ * current device to the driver. */
+ARGCSR_API argcsr_status argcsr_trim_pool(void);
+
+/* ---------------------------------------------------------------------------
+ * Kernel tracing, a profiling aid (off by default).  Between
+ * argcsr_trace_begin and argcsr_trace_end the library records a CUDA event
+ * pair around every kernel it launches, on the stream it launches on.
+ * argcsr_trace_end waits for the recorded events and sums the durations per
+ * kernel; argcsr_trace_kernel then reads, for kernel index 0 .. count-1, its
+ * name (static storage), number of launches and total milliseconds.
+ * ------------------------------------------------------------------------ */
+ARGCSR_API argcsr_status argcsr_trace_begin(void);
+ARGCSR_API argcsr_status argcsr_trace_end(void);
+ARGCSR_API int32_t argcsr_trace_kernel_count(void);
+ARGCSR_API argcsr_status argcsr_trace_kernel(int32_t index, const char **name, int64_t *launches,
+                                             double *total_ms);
+
+/* Library version string, e.g. "argcsr 0.1 sm_103a". */
+ARGCSR_API const char *argcsr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ARGCSR_H */

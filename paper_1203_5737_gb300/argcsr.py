@@ -1,0 +1,332 @@
+"""ctypes binding of libargcsr.so -- the C ABI declared in include/argcsr.h.
+
+The functions named ``argcsr_*`` mirror the C calls one to one and take raw
+integers for pointers and streams.  ``ArgCsrMatrix`` and
+``baseline_csr_spmv`` are conveniences over them for torch CUDA tensors:
+they only check arguments, allocate outputs with torch and pass pointers --
+every computation runs in the library's CUDA kernels.  There is no CPU
+fallback: if the library is not built, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libargcsr.so")
+
+ARGCSR_OK, ARGCSR_EINVAL, ARGCSR_ENOMEM, ARGCSR_ECUDA, ARGCSR_EOVERFLOW, ARGCSR_ENOTSUP = 0, -1, -2, -3, -4, -5
+ARGCSR_F64, ARGCSR_F32, ARGCSR_BF16 = 0, 1, 2
+
+
+class argcsr_params(ctypes.Structure):
+    _fields_ = [("group_size", ctypes.c_int32), ("desired_chunk_size", ctypes.c_int32),
+                ("vec_width", ctypes.c_int32)]
+
+
+class argcsr_info_t(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int32), ("n_cols", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("n_groups", ctypes.c_int64), ("n_slots", ctypes.c_int64),
+                ("group_size", ctypes.c_int32), ("desired_chunk_size", ctypes.c_int32),
+                ("vec_width", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("spmv_bytes", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ArgcsrError(RuntimeError):
+    def __init__(self, status, where):
+        msg = f"{where}: {argcsr_status_string(status)}"
+        detail = argcsr_last_error_message()
+        if detail:
+            msg += f" [{detail}]"
+        super().__init__(msg)
+        self.status = status
+
+
+_lib = None
+
+# name -> (restype, argtypes); the declarations of include/argcsr.h
+_P, _I32, _I64, _U64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+_SIGNATURES = {
+    "argcsr_create_from_csr": (ctypes.c_int, [_I32, _I32, _I64, _P, _P, _P, ctypes.c_int,
+                                              ctypes.POINTER(argcsr_params), _P, ctypes.POINTER(_P)]),
+    "argcsr_spmv": (ctypes.c_int, [_P, _P, _P, _P]),
+    "argcsr_info": (ctypes.c_int, [_P, ctypes.POINTER(argcsr_info_t)]),
+    "argcsr_export": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "argcsr_device_arrays": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                            ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+    "argcsr_destroy": (ctypes.c_int, [_P, _P]),
+    "argcsr_baseline_csr_spmv": (ctypes.c_int, [_I32, _I32, _I64, _P, _P, _P, ctypes.c_int, _I32,
+                                                _P, _P, _P]),
+    "argcsr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "argcsr_last_error_message": (ctypes.c_char_p, []),
+    "argcsr_launch_count": (_U64, []),
+    "argcsr_trim_pool": (ctypes.c_int, []),
+    "argcsr_version": (ctypes.c_char_p, []),
+    "argcsr_trace_begin": (ctypes.c_int, []),
+    "argcsr_trace_end": (ctypes.c_int, []),
+    "argcsr_trace_kernel_count": (ctypes.c_int32, []),
+    "argcsr_trace_kernel": (ctypes.c_int, [_I32, ctypes.POINTER(ctypes.c_char_p),
+                                           ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_double)]),
+}
+
+
+def load_library(path: str = LIB_PATH):
+    """dlopen libargcsr.so (no GPU needed for the load itself)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is not built; run paper_1203_5737_gb300.build.build() "
+                               "(there is no CPU fallback)")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(st, where):
+    if st != ARGCSR_OK:
+        raise ArgcsrError(st, where)
+
+
+# ---------------------------------------------------------------------------
+# One-to-one wrappers of the C calls (raw pointers / streams as ints)
+# ---------------------------------------------------------------------------
+
+def argcsr_status_string(status: int) -> str:
+    return load_library().argcsr_status_string(status).decode()
+
+
+def argcsr_last_error_message() -> str:
+    return load_library().argcsr_last_error_message().decode()
+
+
+def argcsr_launch_count() -> int:
+    return int(load_library().argcsr_launch_count())
+
+
+def argcsr_trim_pool() -> None:
+    _check(load_library().argcsr_trim_pool(), "argcsr_trim_pool")
+
+
+def argcsr_version() -> str:
+    return load_library().argcsr_version().decode()
+
+
+def argcsr_trace_begin() -> None:
+    _check(load_library().argcsr_trace_begin(), "argcsr_trace_begin")
+
+
+def argcsr_trace_end() -> None:
+    _check(load_library().argcsr_trace_end(), "argcsr_trace_end")
+
+
+def argcsr_trace_kernel_count() -> int:
+    return int(load_library().argcsr_trace_kernel_count())
+
+
+def argcsr_trace_kernel(index: int):
+    """(name, launches, total_ms) of traced kernel ``index``."""
+    name, n, ms = ctypes.c_char_p(), ctypes.c_int64(), ctypes.c_double()
+    _check(load_library().argcsr_trace_kernel(index, ctypes.byref(name), ctypes.byref(n),
+                                              ctypes.byref(ms)), "argcsr_trace_kernel")
+    return name.value.decode(), n.value, ms.value
+
+
+def trace_summary() -> dict:
+    """{kernel: (launches, total_ms)} of the last trace."""
+    out = {}
+    for i in range(argcsr_trace_kernel_count()):
+        name, n, ms = argcsr_trace_kernel(i)
+        out[name] = (n, ms)
+    return out
+
+
+def argcsr_create_from_csr(n_rows, n_cols, nnz, d_rowPointers, d_columns, d_values, dtype,
+                           group_size, desired_chunk_size, vec_width=1, stream=0) -> int:
+    """Returns the handle (an int); raises ArgcsrError on a non-OK status."""
+    p = argcsr_params(group_size, desired_chunk_size, vec_width)
+    out = ctypes.c_void_p()
+    st = load_library().argcsr_create_from_csr(n_rows, n_cols, nnz, d_rowPointers, d_columns,
+                                               d_values, dtype, ctypes.byref(p), stream,
+                                               ctypes.byref(out))
+    _check(st, "argcsr_create_from_csr")
+    return out.value
+
+
+def argcsr_spmv(A, d_x, d_y, stream=0) -> None:
+    _check(load_library().argcsr_spmv(A, d_x, d_y, stream), "argcsr_spmv")
+
+
+def argcsr_info(A) -> argcsr_info_t:
+    info = argcsr_info_t()
+    _check(load_library().argcsr_info(A, ctypes.byref(info)), "argcsr_info")
+    return info
+
+
+def argcsr_export(A, h_groupInfo, h_threadsMapping, h_columns, h_values) -> None:
+    _check(load_library().argcsr_export(A, h_groupInfo, h_threadsMapping, h_columns, h_values),
+           "argcsr_export")
+
+
+def argcsr_device_arrays(A):
+    ptrs = [ctypes.c_void_p() for _ in range(4)]
+    _check(load_library().argcsr_device_arrays(A, *[ctypes.byref(p) for p in ptrs]),
+           "argcsr_device_arrays")
+    return tuple(p.value for p in ptrs)
+
+
+def argcsr_destroy(A, stream=0) -> None:
+    _check(load_library().argcsr_destroy(A, stream), "argcsr_destroy")
+
+
+def argcsr_baseline_csr_spmv(n_rows, n_cols, nnz, d_rowPointers, d_columns, d_values, dtype,
+                             variant, d_x, d_y, stream=0) -> None:
+    _check(load_library().argcsr_baseline_csr_spmv(n_rows, n_cols, nnz, d_rowPointers, d_columns,
+                                                   d_values, dtype, variant, d_x, d_y, stream),
+           "argcsr_baseline_csr_spmv")
+
+
+# ---------------------------------------------------------------------------
+# torch conveniences
+# ---------------------------------------------------------------------------
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dtype_code(t):
+    torch = _torch()
+    if t == torch.float64:
+        return ARGCSR_F64
+    if t == torch.float32:
+        return ARGCSR_F32
+    if t == torch.bfloat16:
+        return ARGCSR_BF16
+    raise ValueError(f"unsupported value dtype {t}")
+
+
+def _vector_dtype(code):
+    torch = _torch()
+    return torch.float64 if code == ARGCSR_F64 else torch.float32
+
+
+def _ptr(t):
+    return t.data_ptr() if t is not None and t.numel() else None
+
+
+def _stream(stream):
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+def _check_cuda(name, t, dtype=None):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+
+
+class ArgCsrMatrix:
+    """An ARG-CSR matrix on the GPU, built from torch CSR tensors."""
+
+    def __init__(self, handle, stream=None):
+        self._h = handle
+        info = argcsr_info(handle)
+        self.n_rows, self.n_cols = info.n_rows, info.n_cols
+        self.dtype_code = info.dtype
+        self.vector_dtype = _vector_dtype(info.dtype)
+
+    @classmethod
+    def from_csr(cls, rowPointers, columns, values, n_cols, group_size=32, desired_chunk_size=4,
+                 vec_width=1, stream=None):
+        torch = _torch()
+        _check_cuda("rowPointers", rowPointers, torch.int32)
+        _check_cuda("columns", columns, torch.int32)
+        _check_cuda("values", values)
+        n_rows = rowPointers.numel() - 1
+        nnz = columns.numel()
+        if values.numel() != nnz:
+            raise ValueError("values and columns differ in length")
+        h = argcsr_create_from_csr(n_rows, n_cols, nnz, _ptr(rowPointers), _ptr(columns),
+                                   _ptr(values), _dtype_code(values.dtype), group_size,
+                                   desired_chunk_size, vec_width, _stream(stream))
+        return cls(h)
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("matrix is closed")
+        return self._h
+
+    def spmv(self, x, out=None, stream=None):
+        """y = A x (one kernel on the stream)."""
+        torch = _torch()
+        _check_cuda("x", x, self.vector_dtype)
+        if x.numel() != self.n_cols:
+            raise ValueError(f"x has {x.numel()} elements, expected {self.n_cols}")
+        if out is None:
+            out = torch.empty(self.n_rows, dtype=self.vector_dtype, device=x.device)
+        else:
+            _check_cuda("out", out, self.vector_dtype)
+            if out.numel() != self.n_rows:
+                raise ValueError("out has the wrong length")
+        argcsr_spmv(self.handle, _ptr(x), _ptr(out), _stream(stream))
+        return out
+
+    def info(self) -> dict:
+        return argcsr_info(self.handle).as_dict()
+
+    def export(self) -> dict:
+        """Copy the format's arrays to numpy (synchronous)."""
+        info = argcsr_info(self.handle)
+        vdt = {ARGCSR_F64: np.float64, ARGCSR_F32: np.float32, ARGCSR_BF16: np.uint16}[info.dtype]
+        gi = np.empty((info.n_groups, 4), dtype=np.int32)
+        tm = np.empty(info.n_rows, dtype=np.int32)
+        cols = np.empty(info.n_slots, dtype=np.int32)
+        vals = np.empty(info.n_slots, dtype=vdt)
+        p = lambda a: a.ctypes.data if a.size else None  # noqa: E731
+        argcsr_export(self.handle, p(gi), p(tm), p(cols), p(vals))
+        return {"groupInfo": gi, "threadsMapping": tm, "columns": cols, "values": vals}
+
+    def close(self, stream=None):
+        if self._h is not None:
+            argcsr_destroy(self._h, _stream(stream))
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            if self._h is not None:
+                load_library().argcsr_destroy(self._h, None)
+                self._h = None
+        except Exception:
+            pass
+
+
+def baseline_csr_spmv(rowPointers, columns, values, n_cols, x, variant=1, out=None, stream=None):
+    """Plain CSR SpMV (scalar: variant 0, vector: variant 1) in the library."""
+    torch = _torch()
+    code = _dtype_code(values.dtype)
+    n_rows = rowPointers.numel() - 1
+    if out is None:
+        out = torch.empty(n_rows, dtype=_vector_dtype(code), device=x.device)
+    argcsr_baseline_csr_spmv(n_rows, n_cols, columns.numel(), _ptr(rowPointers), _ptr(columns),
+                             _ptr(values), code, variant, _ptr(x), _ptr(out), _stream(stream))
+    return out

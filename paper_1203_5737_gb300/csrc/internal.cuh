@@ -1,0 +1,86 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "argcsr.h"
+
+namespace argcsr {
+
+// Bits of the device-side validation word written by the conversion kernels.
+enum : unsigned {
+    kBadRowPointers = 1u,  // rowPointers[0] != 0, decreasing, or last != nnz
+    kBadColumn      = 2u,  // a column outside [0, n_cols)
+    kSlotOverflow   = 4u,  // more than 2^31 - 1 slots
+};
+
+// Totals produced on the device during conversion and read back once.
+struct DeviceTotals {
+    unsigned status;
+    unsigned pad;
+    long long n_groups;
+    long long n_slots;
+};
+
+}  // namespace argcsr
+
+struct argcsr_matrix {
+    int device;
+    int32_t n_rows, n_cols;
+    int64_t nnz;
+    int32_t G, D, V;
+    argcsr_dtype dtype;
+    int64_t n_groups, n_slots;
+    int4 *d_groupInfo;          // {firstRow, size, offset, chunkSize}
+    int32_t *d_threadsMapping;  // group-local inclusive prefix of threads per row
+    int32_t *d_columns;         // S slots, -1 = padding
+    void *d_values;             // S slots of dtype, +0.0 = padding
+    int64_t device_bytes;
+};
+
+namespace argcsr {
+
+extern std::atomic<uint64_t> g_launches;
+
+inline void count_launches(uint64_t k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// Tracing: while argcsr_trace_begin() is in effect, a TraceScope records an
+// event pair around the launches made during its lifetime.
+int trace_start(const char *name, cudaStream_t s);
+void trace_stop(int token, cudaStream_t s);
+struct TraceScope {
+    int token;
+    cudaStream_t s;
+    TraceScope(const char *name, cudaStream_t stream) : token(trace_start(name, stream)), s(stream) {}
+    ~TraceScope() { trace_stop(token, s); }
+};
+
+// Record a CUDA error for argcsr_last_error_message(); returns ARGCSR_ECUDA
+// (or ARGCSR_ENOMEM for allocation failures).
+argcsr_status record_cuda(cudaError_t err, const char *where);
+
+// Stream-ordered allocation from the library's per-device pool.
+argcsr_status pool_alloc(void **p, size_t bytes, cudaStream_t s);
+void pool_free(void *p, cudaStream_t s);
+
+inline size_t dtype_size(argcsr_dtype t) {
+    return t == ARGCSR_F64 ? 8 : t == ARGCSR_F32 ? 4 : 2;
+}
+inline size_t vec_size(argcsr_dtype t) {  // element size of x and y
+    return t == ARGCSR_F64 ? 8 : 4;
+}
+
+// Defined in spmv.cu: launch the ARG-CSR SpMV kernel for a handle.
+argcsr_status launch_spmv(const argcsr_matrix *A, const void *x, void *y, cudaStream_t s);
+
+}  // namespace argcsr
+
+#define ARGCSR_CHECK_LAUNCH(where)                                   \
+    do {                                                             \
+        cudaError_t e_ = cudaGetLastError();                         \
+        if (e_ != cudaSuccess) return argcsr::record_cuda(e_, where); \
+    } while (0)

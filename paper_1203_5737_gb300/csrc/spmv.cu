@@ -1,0 +1,217 @@
+// SpMV y = A x on ARG-CSR (Section 4 of Heller & Oberhuber).
+//
+// Semantics follow the paper's kernel: one thread per chunk, each thread
+// sums its chunk's slots in element order (element j of chunk c at
+// offset + j*G + c, or the V-interleaved form), stops at the trailing
+// padding (column -1), and the partial sums of a row's chunks -- the range
+// [threadsMapping[r-1], threadsMapping[r]) -- are added into y[r].
+//
+// GB300 design:
+//  * G = 32: one warp per group, eight groups per 256-thread block.  The
+//    group record is one 16-byte load; the row of each chunk comes from a
+//    bit mask of row ends built with one warp reduction over threadsMapping
+//    (no shared memory, no block barrier); partial sums are combined with a
+//    segmented shuffle scan and the last lane of each row stores y.
+//  * G = 64 / 128: one group per G threads, the paper's shared-memory
+//    reduction (a row's owner thread adds its chunks' partials).
+//  * values/columns are streamed with evict-first loads (each slot is read
+//    once); x is gathered through the read-only path so that its lines stay
+//    in L2; V > 1 turns the per-thread loads into 8/16-byte vector loads.
+//  * the loop over a chunk runs in batches of four elements; a batch whose
+//    last element is padding in every lane of the warp ends the loop (the
+//    paper's early exit when a whole warp reaches artificial zeros).
+#include "internal.cuh"
+
+namespace argcsr {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+template <typename VT> struct AccOf { using type = float; };
+template <> struct AccOf<double> { using type = double; };
+
+__device__ __forceinline__ double widen(double v) { return v; }
+__device__ __forceinline__ float widen(float v) { return v; }
+__device__ __forceinline__ float widen(uint16_t bits) { return __uint_as_float((unsigned)bits << 16); }
+
+// Streaming (evict-first) loads of V consecutive elements, V*sizeof(T) in
+// {2, 4, 8, 16, 32} bytes, from an address aligned to that size.
+template <typename T, int V>
+__device__ __forceinline__ void ld_stream(const T *p, T (&out)[V]) {
+    constexpr int B = (int)sizeof(T) * V;
+    if constexpr (B == 2) {
+        unsigned short u = __ldcs(reinterpret_cast<const unsigned short *>(p));
+        memcpy(out, &u, 2);
+    } else if constexpr (B == 4) {
+        unsigned u = __ldcs(reinterpret_cast<const unsigned *>(p));
+        memcpy(out, &u, 4);
+    } else if constexpr (B == 8) {
+        uint2 u = __ldcs(reinterpret_cast<const uint2 *>(p));
+        memcpy(out, &u, 8);
+    } else if constexpr (B == 16) {
+        uint4 u = __ldcs(reinterpret_cast<const uint4 *>(p));
+        memcpy(out, &u, 16);
+    } else {
+        static_assert(B == 32, "unsupported vector width");
+        uint4 u0 = __ldcs(reinterpret_cast<const uint4 *>(p));
+        uint4 u1 = __ldcs(reinterpret_cast<const uint4 *>(p) + 1);
+        memcpy(out, &u0, 16);
+        memcpy(reinterpret_cast<char *>(out) + 16, &u1, 16);
+    }
+}
+
+// Sum of one chunk: C/V blocks of V elements; block b of chunk c starts at
+// base + b*G*V + c*V.  Lanes that own no row (free chunks) load nothing.
+// Every lane of the warp must call this (it votes on early exit).
+template <int G, typename VT, int V>
+__device__ __forceinline__ typename AccOf<VT>::type
+chunk_sum(const int *__restrict__ cols, const VT *__restrict__ vals,
+          const typename AccOf<VT>::type *__restrict__ x, long long base, int C, bool owns) {
+    using Acc = typename AccOf<VT>::type;
+    constexpr int U = V >= 4 ? 1 : 4 / V;   // blocks per batch: 4 elements
+    Acc sum = 0;
+    const int nb = C / V;
+    const int *cp = cols + base;
+    const VT *vp = vals + base;
+    for (int b = 0; b < nb; b += U) {
+        int c[U][V];
+        VT v[U][V];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (owns && b + u < nb) {
+                ld_stream<int, V>(cp + (long long)(b + u) * G * V, c[u]);
+            } else {
+#pragma unroll
+                for (int e = 0; e < V; ++e) c[u][e] = -1;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (c[u][0] >= 0) {
+                ld_stream<VT, V>(vp + (long long)(b + u) * G * V, v[u]);
+            } else {
+#pragma unroll
+                for (int e = 0; e < V; ++e) v[u][e] = VT(0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                if (c[u][e] >= 0) sum = fma(widen(v[u][e]), __ldg(x + c[u][e]), sum);
+            }
+        }
+        if (__all_sync(FULL, c[U - 1][V - 1] < 0)) break;
+    }
+    return sum;
+}
+
+// G = 32: one warp per group.
+template <typename VT, int V>
+__global__ void __launch_bounds__(256)
+k_spmv_g32(long long nGroups, const int4 *__restrict__ gi, const int *__restrict__ tm,
+           const int *__restrict__ cols, const VT *__restrict__ vals,
+           const typename AccOf<VT>::type *__restrict__ x, typename AccOf<VT>::type *__restrict__ y) {
+    using Acc = typename AccOf<VT>::type;
+    const int lane = threadIdx.x & 31;
+    const long long g = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (g >= nGroups) return;  // warp-uniform
+    const int4 info = __ldg(gi + g);  // firstRow, size, offset, chunkSize
+    const int first = info.x, size = info.y, C = info.w;
+    const int end = lane < size ? __ldg(tm + first + lane) : 0;
+    // bit k set <=> chunk k is the last chunk of a row
+    const unsigned ends = __reduce_or_sync(FULL, lane < size ? 1u << (end - 1) : 0u);
+    const unsigned below = ends & ((1u << lane) - 1u);
+    const int row = __popc(below);          // local row of this lane's chunk
+    const bool owns = row < size;           // false for free chunks
+    Acc sum = chunk_sum<32, VT, V>(cols, vals, x, (long long)info.z + lane * V, C, owns);
+    // segmented inclusive scan: add partials of lanes of the same row
+    const int segStart = below ? 32 - __clz(below) : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const Acc v = __shfl_up_sync(FULL, sum, o);
+        if (lane - o >= segStart) sum += v;
+    }
+    if (owns && ((ends >> lane) & 1u)) y[first + row] = sum;
+}
+
+// G = 64 or 128: one group per G threads, 256 / G groups per block.
+template <int G, typename VT, int V>
+__global__ void __launch_bounds__(256)
+k_spmv_block(long long nGroups, const int4 *__restrict__ gi, const int *__restrict__ tm,
+             const int *__restrict__ cols, const VT *__restrict__ vals,
+             const typename AccOf<VT>::type *__restrict__ x, typename AccOf<VT>::type *__restrict__ y) {
+    using Acc = typename AccOf<VT>::type;
+    constexpr int GPB = 256 / G;
+    __shared__ Acc partial[256];
+    __shared__ int rowOf[256];
+    const int sub = threadIdx.x / G, c = threadIdx.x % G;
+    const long long g = (long long)blockIdx.x * GPB + sub;
+    const bool valid = g < nGroups;
+    const int4 info = valid ? __ldg(gi + g) : make_int4(0, 0, 0, 0);
+    const int first = info.x, size = info.y, C = info.w;
+    rowOf[threadIdx.x] = -1;
+    __syncthreads();
+    int begin = 0, end = 0;
+    if (c < size) {
+        end = __ldg(tm + first + c);
+        begin = c ? __ldg(tm + first + c - 1) : 0;
+        for (int k = begin; k < end; ++k) rowOf[sub * G + k] = c;
+    }
+    __syncthreads();
+    const bool owns = rowOf[threadIdx.x] >= 0;
+    // warps never straddle groups (G is a multiple of 32), so C is warp-uniform
+    partial[threadIdx.x] = chunk_sum<G, VT, V>(cols, vals, x, (long long)info.z + c * V, C, owns);
+    __syncthreads();
+    if (c < size) {
+        Acc s = 0;
+        for (int k = begin; k < end; ++k) s += partial[sub * G + k];
+        y[first + c] = s;
+    }
+}
+
+template <typename VT, int V>
+argcsr_status launch_typed(const argcsr_matrix *A, const void *x, void *y, cudaStream_t s) {
+    using Acc = typename AccOf<VT>::type;
+    const long long ng = A->n_groups;
+    const auto *gi = A->d_groupInfo;
+    const auto *tm = A->d_threadsMapping;
+    const auto *cols = A->d_columns;
+    const auto *vals = static_cast<const VT *>(A->d_values);
+    const auto *xx = static_cast<const Acc *>(x);
+    auto *yy = static_cast<Acc *>(y);
+    TraceScope t(A->G == 32 ? "k_spmv_g32" : "k_spmv_block", s);
+    switch (A->G) {
+        case 32: k_spmv_g32<VT, V><<<(unsigned)((ng + 7) / 8), 256, 0, s>>>(ng, gi, tm, cols, vals, xx, yy); break;
+        case 64: k_spmv_block<64, VT, V><<<(unsigned)((ng + 3) / 4), 256, 0, s>>>(ng, gi, tm, cols, vals, xx, yy); break;
+        default: k_spmv_block<128, VT, V><<<(unsigned)((ng + 1) / 2), 256, 0, s>>>(ng, gi, tm, cols, vals, xx, yy); break;
+    }
+    count_launches(1);
+    ARGCSR_CHECK_LAUNCH("argcsr_spmv kernel");
+    return ARGCSR_OK;
+}
+
+template <typename VT>
+argcsr_status launch_v(const argcsr_matrix *A, const void *x, void *y, cudaStream_t s) {
+    switch (A->V) {
+        case 1: return launch_typed<VT, 1>(A, x, y, s);
+        case 2: return launch_typed<VT, 2>(A, x, y, s);
+        default: return launch_typed<VT, 4>(A, x, y, s);
+    }
+}
+
+}  // namespace
+
+argcsr_status launch_spmv(const argcsr_matrix *A, const void *x, void *y, cudaStream_t s) {
+    if (A->n_groups == 0) {
+        // every group is empty only if there are no rows
+        return ARGCSR_OK;
+    }
+    switch (A->dtype) {
+        case ARGCSR_F64: return launch_v<double>(A, x, y, s);
+        case ARGCSR_F32: return launch_v<float>(A, x, y, s);
+        default: return launch_v<uint16_t>(A, x, y, s);
+    }
+}
+
+}  // namespace argcsr

@@ -1,0 +1,104 @@
+"""The C-ABI library builds, loads and exports every declared symbol.
+
+These run without a GPU: only calls that fail argument checks before any
+CUDA work, and the status/version helpers, are exercised here.
+"""
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+from conftest import ROOT
+
+from paper_1203_5737_gb300 import argcsr as api
+from paper_1203_5737_gb300 import build as b
+
+
+def _declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        # ARGCSR_API <return type> <name>(
+        for m in re.finditer(r"ARGCSR_API\s+[\w\s\*]+?\b(\w+)\s*\(", text):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    b.build()
+    return api.load_library()
+
+
+def test_headers_declare_the_boundary():
+    names = _declared_symbols()
+    for required in ("argcsr_create_from_csr", "argcsr_spmv", "argcsr_destroy", "argcsr_info",
+                     "argcsr_export", "argcsr_baseline_csr_spmv"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    declared = _declared_symbols()
+    out = subprocess.run(["nm", "-D", "--defined-only", b.LIB], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = declared - exported
+    assert not missing, f"declared but not exported: {sorted(missing)}"
+    # nothing else leaks out of the library under an argcsr_ name
+    assert {s for s in exported if s.startswith("argcsr")} == declared
+    for name in declared:
+        assert hasattr(lib, name)
+
+
+def test_binding_covers_every_symbol():
+    assert set(api._SIGNATURES) == _declared_symbols()
+
+
+def test_status_strings_and_version(lib):
+    assert api.argcsr_status_string(0) == "ARGCSR_OK"
+    for code in (-1, -2, -3, -4, -5):
+        assert api.argcsr_status_string(code).startswith("ARGCSR_E")
+    assert "sm_103a" in api.argcsr_version()
+    assert api.argcsr_launch_count() >= 0
+
+
+def test_argument_checks_without_gpu(lib):
+    P = api.argcsr_params(32, 4, 1)
+    out = ctypes.c_void_p(123)
+    # invalid group size, chunk size, vector width, dtype, sizes: all EINVAL
+    for params in ((16, 4, 1), (32, 0, 1), (32, 4, 3), (256, 1, 1)):
+        p = api.argcsr_params(*params)
+        assert lib.argcsr_create_from_csr(10, 10, 0, 8, None, None, 0, ctypes.byref(p), None,
+                                          ctypes.byref(out)) == api.ARGCSR_EINVAL
+        assert out.value is None
+    assert lib.argcsr_create_from_csr(-1, 10, 0, 8, None, None, 0, ctypes.byref(P), None,
+                                      ctypes.byref(out)) == api.ARGCSR_EINVAL
+    assert lib.argcsr_create_from_csr(10, 10, 5, 8, None, None, 0, ctypes.byref(P), None,
+                                      ctypes.byref(out)) == api.ARGCSR_EINVAL
+    assert lib.argcsr_create_from_csr(10, 10, 0, 8, None, None, 7, ctypes.byref(P), None,
+                                      ctypes.byref(out)) == api.ARGCSR_EINVAL
+    assert lib.argcsr_create_from_csr(10, 10, 0, None, None, None, 0, ctypes.byref(P), None,
+                                      ctypes.byref(out)) == api.ARGCSR_EINVAL
+    assert lib.argcsr_create_from_csr(10, 10, 0, 8, None, None, 0, None, None,
+                                      ctypes.byref(out)) == api.ARGCSR_EINVAL
+    assert lib.argcsr_spmv(None, None, None, None) == api.ARGCSR_EINVAL
+    assert lib.argcsr_info(None, None) == api.ARGCSR_EINVAL
+    assert lib.argcsr_export(None, None, None, None, None) == api.ARGCSR_EINVAL
+    assert lib.argcsr_destroy(None, None) == api.ARGCSR_OK
+    assert lib.argcsr_baseline_csr_spmv(10, 10, 0, 8, None, None, 0, 2, None, None, None) == api.ARGCSR_EINVAL
+    assert lib.argcsr_baseline_csr_spmv(-3, 10, 0, 8, None, None, 0, 0, None, None, None) == api.ARGCSR_EINVAL
+
+
+def test_python_errors_carry_the_status(lib):
+    with pytest.raises(api.ArgcsrError) as e:
+        api.argcsr_spmv(None, None, None)
+    assert e.value.status == api.ARGCSR_EINVAL
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    monkeypatch.setattr(api, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        api.load_library(str(tmp_path / "libargcsr.so"))

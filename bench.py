@@ -1,0 +1,552 @@
+#!/usr/bin/env python3
+"""Benchmark of the ARG-CSR hot path on GB300.
+
+One step = the whole hot path over the uneven-rows FP64 workload: for each
+of its two matrices -- lognormal(2.3, 1.2) row lengths with n = 2,000,000
+and the 7-point Laplacian on a 128^3 grid -- CSR -> ARG-CSR conversion
+(G = 32) followed by one SpMV y = A x, then the handle is freed.  The CSR
+inputs and x are resident in HBM before the timed region starts.
+
+value = algorithmic bytes of the step / step time, where
+  conversion: 4(n+1) + nnz(4+8)            (read the CSR arrays)
+            + 16 groups + 4 n + S (4+8)    (write groupInfo, threadsMapping
+                                            and the S padded slots)
+  SpMV:       nnz(8+4) + 8 n_cols + 8 n + 4 n + 16 groups
+              (values + columns + x + y + threadsMapping + groupInfo;
+               padding not counted)
+The SpMV-only rate (the paper's measured kernel) is reported under "spmv",
+beside the plain CSR kernel and cuSPARSE on the same matrices.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With --gpus N > 1 (launched by torchrun) every rank runs an independent
+replica of the workload on its own GPU (the path needs no exchange); value
+sums all ranks' bytes over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "ARG-CSR SpMV GB/s (% HBM peak) vs plain CSR; served CG solves/s, p99 latency"
+WORKLOAD = ("uneven rows FP64: lognormal(2.3,1.2) n=2,000,000 + 3D 7-point Laplacian 128^3; "
+            "CSR->ARG-CSR (G=32) + SpMV per matrix")
+GROUP_SIZE = 32
+MATRICES = (("lognormal_2m", 4), ("laplace3d_128", 8))   # (workload, desiredChunkSize)
+SV = 8   # bytes per stored value (FP64)
+SX = 8   # bytes per x / y element
+FALLBACK_HBM_GBS = 6800.0
+L2_BYTES = 129 * 2 ** 20
+
+
+# ---------------------------------------------------------------------------
+# byte model
+# ---------------------------------------------------------------------------
+
+def conversion_bytes(n, nnz, groups, slots):
+    return 4 * (n + 1) + nnz * (4 + SV) + 16 * groups + 4 * n + slots * (4 + SV)
+
+
+def spmv_bytes(n, n_cols, nnz, groups):
+    return nnz * (SV + 4) + n_cols * SX + n * SX + 4 * n + 16 * groups
+
+
+def csr_spmv_bytes(n, n_cols, nnz):
+    return nnz * (SV + 4) + n_cols * SX + n * SX + 4 * (n + 1)
+
+
+def kernel_bytes(kernel, n, n_cols, nnz, groups, slots):
+    """Algorithmic bytes of one launch of each library kernel on one matrix."""
+    return {
+        "k_next_delta": 4 * (n + 1) + n,
+        "k_tile_walk": n,
+        "k_groups": 4 * (n + 1) + n + 4 * n + 16 * groups,
+        "k_fill": nnz * (4 + SV) + 4 * (n + 1) + 4 * n + 16 * groups * 2 + slots * (4 + SV),
+        "k_spmv_g32": spmv_bytes(n, n_cols, nnz, groups),
+        "k_spmv_block": spmv_bytes(n, n_cols, nnz, groups),
+    }.get(kernel, 0)
+
+
+# ---------------------------------------------------------------------------
+# multi-rank plumbing (replicas only)
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def dist_init(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(value, world, device="cpu"):
+    """Max of a float over all ranks (identity for one rank)."""
+    if world == 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(value, world, device="cpu"):
+    if world == 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        mx = max(float(r[2]) for r in rows)
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        loaded = [s for s, r in zip(sm, rows) if s > 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows),
+                "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()),
+                                   default=None)}
+
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1203_5737_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch from profiles/traffic.txt, if they were taken on
+    the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    digest = kernel_source_digest()
+    try:
+        with open(path) as f:
+            for line in f:
+                if line.startswith("#") or not line.strip():
+                    continue
+                k, wl, nbytes, dig = line.split()[:4]
+                if k == kernel and wl == "bench" and dig == digest:
+                    return float(nbytes)
+    except OSError:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+class Mat:
+    pass
+
+
+def prepare(name, D, dev, torch, pinned=False):
+    A, x = synth.workload(name)
+    m = Mat()
+    m.name, m.D, m.A = name, D, A
+    m.n, m.n_cols, m.nnz = A.n_rows, A.n_cols, A.nnz
+    m.rp = torch.from_numpy(A.rowPointers).to(dev)
+    m.cols = torch.from_numpy(A.columns).to(dev)
+    m.vals = torch.from_numpy(A.values).to(dev)
+    m.x = torch.from_numpy(x).to(dev)
+    m.y = torch.empty(m.n, dtype=torch.float64, device=dev)
+    m.x_np = x
+    if pinned:
+        m.h_rp = torch.from_numpy(A.rowPointers).pin_memory()
+        m.h_cols = torch.from_numpy(A.columns).pin_memory()
+        m.h_vals = torch.from_numpy(A.values).pin_memory()
+        m.h_x = torch.from_numpy(x).pin_memory()
+        m.h_y = torch.empty(m.n, dtype=torch.float64).pin_memory()
+    return m
+
+
+def run_ours(args):
+    import torch
+    from paper_1203_5737_gb300 import argcsr as api
+    from paper_1203_5737_gb300 import build
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (there is no CPU fallback)")
+    torch.cuda.set_device(local)
+    dist_init(world, "nccl")
+    build.build()
+    api.load_library()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    s = stream.cuda_stream
+    mats = [prepare(name, D, dev, torch, pinned=True) for name, D in MATRICES]
+
+    def convert(m, src=None):
+        rp, cols, vals = src or (m.rp, m.cols, m.vals)
+        return api.argcsr_create_from_csr(m.n, m.n_cols, m.nnz, rp.data_ptr(), cols.data_ptr(),
+                                          vals.data_ptr(), api.ARGCSR_F64, GROUP_SIZE, m.D, 1, s)
+
+    def step():
+        for m in mats:
+            h = convert(m)
+            api.argcsr_spmv(h, m.x.data_ptr(), m.y.data_ptr(), s)
+            api.argcsr_destroy(h, s)
+
+    # sizes of the converted matrices (identical every step)
+    for m in mats:
+        h = convert(m)
+        info = api.argcsr_info(h)
+        m.groups, m.slots = info.n_groups, info.n_slots
+        api.argcsr_destroy(h, s)
+        m.step_bytes = (conversion_bytes(m.n, m.nnz, m.groups, m.slots)
+                        + spmv_bytes(m.n, m.n_cols, m.nnz, m.groups))
+    step_bytes = sum(m.step_bytes for m in mats)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    launches0 = api.argcsr_launch_count()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    api.argcsr_trace_begin()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    api.argcsr_trace_end()
+    clocks = sampler.stop()
+    barrier(world)
+    launches = api.argcsr_launch_count() - launches0
+    ms = e0.elapsed_time(e1)
+    ms_max = reduce_max(ms, world, dev)
+    total_bytes = reduce_sum(step_bytes * args.steps, world, dev)
+    value = total_bytes / (ms_max * 1e-3) / 1e9
+    trace = api.trace_summary()
+
+    # roofline of the dominant kernel (largest share of traced time)
+    peak, peak_kind = measured_hbm_peak()
+    dominant = max(trace, key=lambda k: trace[k][1])
+    launches_k, ms_k = trace[dominant]
+    per_step = sum(kernel_bytes(dominant, m.n, m.n_cols, m.nnz, m.groups, m.slots) for m in mats)
+    kbytes = per_step * args.steps
+    achieved = kbytes / (ms_k * 1e-3) / 1e9
+    traffic = ncu_traffic(dominant)
+    roofline = {"bound": "hbm", "kernel": dominant, "achieved": round(achieved, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": traffic, "peak_source": peak_kind,
+                "bytes_per_launch": round(kbytes / launches_k),
+                "avg_launch_us": round(ms_k * 1e3 / launches_k, 2)}
+    total_traced = sum(v[1] for v in trace.values())
+    kernels = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / total_traced, 4)}
+               for k, v in sorted(trace.items(), key=lambda kv: -kv[1][1])}
+
+    # SpMV alone (the paper's measured operation), baselines on the same GPU
+    spmv = {}
+    spmv_bytes_all, spmv_ms_all = 0, 0.0
+    baselines = {"csr_vector": {}, "csr_scalar": {}, "cusparse": {}}
+    for m in mats:
+        h = convert(m)
+        reps = max(20, args.steps * 5)
+        for _ in range(3):
+            api.argcsr_spmv(h, m.x.data_ptr(), m.y.data_ptr(), s)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            api.argcsr_spmv(h, m.x.data_ptr(), m.y.data_ptr(), s)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b) / reps
+        nbytes = spmv_bytes(m.n, m.n_cols, m.nnz, m.groups)
+        spmv[m.name] = {"us": round(t * 1e3, 2), "gbs": round(nbytes / (t * 1e-3) / 1e9, 1),
+                        "frac": round(nbytes / (t * 1e-3) / 1e9 / peak, 4), "D": m.D,
+                        "slots_per_nnz": round(m.slots / m.nnz, 4),
+                        "gflops": round(2 * m.nnz / (t * 1e-3) / 1e9, 1)}
+        spmv_bytes_all += nbytes
+        spmv_ms_all += t
+        api.argcsr_destroy(h, s)
+        cbytes = csr_spmv_bytes(m.n, m.n_cols, m.nnz)
+        for variant, key in ((1, "csr_vector"), (0, "csr_scalar")):
+            def run_csr():
+                api.argcsr_baseline_csr_spmv(m.n, m.n_cols, m.nnz, m.rp.data_ptr(), m.cols.data_ptr(),
+                                             m.vals.data_ptr(), api.ARGCSR_F64, variant,
+                                             m.x.data_ptr(), m.y.data_ptr(), s)
+            baselines[key][m.name] = _time_gbs(torch, stream, run_csr, cbytes, reps)
+        try:
+            Acsr = torch.sparse_csr_tensor(m.rp, m.cols, m.vals, size=(m.n, m.n_cols))
+            baselines["cusparse"][m.name] = _time_gbs(torch, stream, lambda: torch.mv(Acsr, m.x),
+                                                      cbytes, reps)
+        except Exception as exc:  # report, do not fail the bench
+            baselines["cusparse"][m.name] = {"error": str(exc)[:120]}
+    spmv["combined"] = {"gbs": round(spmv_bytes_all / (spmv_ms_all * 1e-3) / 1e9, 1),
+                        "frac": round(spmv_bytes_all / (spmv_ms_all * 1e-3) / 1e9 / peak, 4)}
+
+    # end to end: pinned host CSR + x in, y out, through the public API
+    h2d = sum(4 * (m.n + 1) + m.nnz * (4 + SV) + m.n_cols * SX for m in mats)
+    d2h = sum(m.n * SX for m in mats)
+
+    def step_e2e():
+        for m in mats:
+            m.rp.copy_(m.h_rp, non_blocking=True)
+            m.cols.copy_(m.h_cols, non_blocking=True)
+            m.vals.copy_(m.h_vals, non_blocking=True)
+            m.x.copy_(m.h_x, non_blocking=True)
+            h = convert(m)
+            api.argcsr_spmv(h, m.x.data_ptr(), m.y.data_ptr(), s)
+            api.argcsr_destroy(h, s)
+            m.h_y.copy_(m.y, non_blocking=True)
+
+    for _ in range(2):
+        step_e2e()
+    torch.cuda.synchronize()
+    barrier(world)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(3, args.steps // 2)
+    a.record(stream)
+    for _ in range(e2e_steps):
+        step_e2e()
+    b.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    e2e_ms = reduce_max(a.elapsed_time(b), world, dev)
+    e2e_value = reduce_sum(step_bytes * e2e_steps, world, dev) / (e2e_ms * 1e-3) / 1e9
+    # the result read back to the host is the product
+    y_check = float(np.abs(mats[0].h_y.numpy()).sum())
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(min_seconds=args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "group_size": GROUP_SIZE,
+                       "desired_chunk_size": {m.name: m.D for m in mats},
+                       "n_rows": {m.name: m.n for m in mats}, "nnz": {m.name: m.nnz for m in mats},
+                       "groups": {m.name: m.groups for m in mats},
+                       "slots": {m.name: m.slots for m in mats},
+                       "bytes_per_step": step_bytes,
+                       "l2": f"inputs larger than L2 ({step_bytes / 2**20:.0f} MiB per step "
+                             f"vs {L2_BYTES / 2**20:.0f} MiB L2); no flush",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms / e2e_steps, 4),
+                    "y_abs_sum": y_check},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "spmv": spmv,
+            "baselines": baselines,
+            "kernels": kernels,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def _time_gbs(torch, stream, fn, nbytes, reps):
+    for _ in range(3):
+        fn()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    t = a.elapsed_time(b) / reps
+    return {"us": round(t * 1e3, 2), "gbs": round(nbytes / (t * 1e-3) / 1e9, 1)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def _row_prefix(A, rows):
+    """The first ``rows`` rows of A (all columns): a bounded sample with the
+    same row-length distribution."""
+    if rows >= A.n_rows:
+        return A
+    nnz = int(A.rowPointers[rows])
+    return synth.Csr(rows, A.n_cols, A.rowPointers[:rows + 1], A.columns[:nnz], A.values[:nnz],
+                     A.name + f"[:{rows}]")
+
+
+def oracle_step(samples):
+    """Conversion + ARG-CSR SpMV of every sampled matrix with the CPU oracle;
+    returns the step's algorithmic bytes."""
+    import oracle
+    nbytes = 0
+    for A, x, D in samples:
+        M = oracle.convert(A, GROUP_SIZE, D)
+        oracle.argcsr_spmv(M, x)
+        nbytes += (conversion_bytes(A.n_rows, A.nnz, M.n_groups, M.n_slots)
+                   + spmv_bytes(A.n_rows, A.n_cols, A.nnz, M.n_groups))
+    return nbytes
+
+
+def _samples(fraction):
+    out = []
+    for name, D in MATRICES:
+        A, x = synth.workload(name)
+        rows = max(1, int(A.n_rows * fraction))
+        out.append((_row_prefix(A, rows), x, D))
+    return out
+
+
+def cpu_baseline(min_seconds=10.0, fraction=1.0):
+    import oracle
+    oracle.build()
+    samples = _samples(fraction)
+    nbytes, elapsed, reps = 0, 0.0, 0
+    while elapsed < min_seconds and reps < 20:
+        t0 = time.perf_counter()
+        nbytes += oracle_step(samples)
+        elapsed += time.perf_counter() - t0
+        reps += 1
+    rows = "+".join(f"{A.n_rows}" for A, _, _ in samples)
+    return {"value": round(nbytes / elapsed / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{reps} x the step on rows {rows} of the two matrices "
+                      f"({elapsed:.1f} s, single-threaded C oracle)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    # keep the whole run within a few minutes: one step costs ~2-4 s at full size
+    fraction = min(1.0, 30.0 / max(1, args.steps + args.warmup))
+    samples = _samples(fraction)
+    for _ in range(args.warmup):
+        oracle_step(samples)
+    t0 = time.perf_counter()
+    nbytes = 0
+    for _ in range(args.steps):
+        nbytes += oracle_step(samples)
+    elapsed = time.perf_counter() - t0
+    value = nbytes / elapsed / 1e9
+    rows = "+".join(f"{A.n_rows}" for A, _, _ in samples)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(elapsed * 1e3 / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "group_size": GROUP_SIZE,
+                   "desired_chunk_size": {n: d for n, d in MATRICES},
+                   "sample_rows": rows, "parallelism": "host, 1 core"},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"each step: rows {rows} of the two matrices "
+                                   f"(fraction {fraction:.3f})"},
+        "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = p.parse_args(argv)
+    args.warmup = max(3, args.warmup)   # at least three untimed warm-up steps
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,114 @@
+"""Host-side logic of bench.py, on the CPU: the byte model, the clock parser,
+the multi-rank reduction (two gloo ranks) and the reference arm's oracle step."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+import bench
+import oracle
+import synth
+
+
+def test_byte_model_by_hand():
+    # n=3 rows, 4 columns, 5 nonzeros, 1 group, 64 slots, FP64
+    assert bench.spmv_bytes(3, 4, 5, 1) == 5 * 12 + 4 * 8 + 3 * 8 + 3 * 4 + 16
+    assert bench.conversion_bytes(3, 5, 1, 64) == 4 * 4 + 5 * 12 + 16 + 3 * 4 + 64 * 12
+    assert bench.csr_spmv_bytes(3, 4, 5) == 5 * 12 + 4 * 8 + 3 * 8 + 4 * 4
+
+
+def test_kernel_bytes_cover_the_traced_kernels():
+    for k in ("k_next_delta", "k_tile_walk", "k_groups", "k_fill", "k_spmv_g32", "k_spmv_block"):
+        assert bench.kernel_bytes(k, 10, 10, 30, 2, 64) > 0
+    assert bench.kernel_bytes("k_spmv_g32", 10, 10, 30, 2, 64) == bench.spmv_bytes(10, 10, 30, 2)
+
+
+def test_clock_parser(tmp_path, monkeypatch):
+    s = bench.ClockSampler(0)
+    s.path = str(tmp_path / "c.csv")
+    with open(s.path, "w") as f:
+        f.write("0, 1965, 2070, 900.5, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+        f.write("0, 1980, 2070, 1000.0, 0x4, Not Active, Not Active, Not Active, Active\n")
+        f.write("0, 300, 2070, 150.0, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+
+    class P:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    s.proc = P()
+    s.out = open(os.devnull, "w")
+    r = s.stop()
+    assert r["sm_mhz"] == pytest.approx(1972.5)   # idle sample excluded
+    assert r["sm_max_mhz"] == 2070
+    assert r["reasons"] == ["sw_power_cap"]
+    assert r["power_w_max"] == 1000.0
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    import bench as b
+    r, w, _ = b.dist_env()
+    b.dist_init(w, "gloo")
+    b.barrier(w)
+    mx = b.reduce_max(10.0 * (r + 1), w)
+    sm = b.reduce_sum(r + 1, w)
+    b.barrier(w)
+    import torch.distributed as dist
+    dist.destroy_process_group()
+    q.put((r, mx, sm))
+
+
+def test_two_rank_reduction_gloo():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    got = sorted(q.get(timeout=10) for _ in range(2))
+    # max over ranks is the slowest rank; the sum adds every replica's units
+    assert got == [(0, 20.0, 3.0), (1, 20.0, 3.0)]
+
+
+def test_single_rank_is_identity():
+    assert bench.reduce_max(3.5, 1) == 3.5
+    assert bench.reduce_sum(7, 1) == 7.0
+
+
+def test_reference_step_on_a_small_sample():
+    oracle.build()
+    A = synth.lognormal_rows(5000, seed_structure=3)
+    x = synth.uniform_vector(A.n_cols, 1)
+    nbytes = bench.oracle_step([(A, x, 4)])
+    M = oracle.convert(A, 32, 4)
+    assert nbytes == (bench.conversion_bytes(A.n_rows, A.nnz, M.n_groups, M.n_slots)
+                      + bench.spmv_bytes(A.n_rows, A.n_cols, A.nnz, M.n_groups))
+
+
+def test_row_prefix_sample():
+    A = synth.random_csr(100, 50, 2)
+    B = bench._row_prefix(A, 10)
+    assert B.n_rows == 10 and B.nnz == A.rowPointers[10]
+    assert np.array_equal(B.columns, A.columns[:B.nnz])
+
+
+def test_reference_arm_other_ranks_do_no_work(monkeypatch, capsys):
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    bench.main(["--impl", "reference", "--steps", "1", "--warmup", "3"])
+    assert capsys.readouterr().out == ""

@@ -164,6 +164,56 @@ ARGCSR_API argcsr_status argcsr_device_arrays(argcsr_t A, const int32_t **d_grou
 ARGCSR_API argcsr_status argcsr_destroy(argcsr_t A, argcsr_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * argcsr_convert_noalloc -- the CSR -> ARG-CSR conversion of
+ * argcsr_create_from_csr for callers that cannot allocate device memory.
+ * The paper has no counterpart; this is a library facility.
+ *
+ * Who needs it: code whose device memory is all handed out up front and
+ * owned by someone else -- a framework arena or caching allocator that must
+ * stay the only allocator in the process, a service under a hard per-process
+ * memory cap, or a latency-critical loop where cudaMalloc/cudaFree would
+ * stall the device.  Such callers can still size and own their outputs.
+ *
+ * What it does not do: call cudaMalloc, cudaFree, a memory pool, or any
+ * allocating library routine.  All intermediate arrays live in one
+ * file-scope __device__ array of ARGCSR_NOALLOC_SCRATCH_BYTES bytes, which
+ * every GPU that loads this library holds until the process exits.  That
+ * caps the matrix at ARGCSR_NOALLOC_MAX_ROWS rows; more rows return
+ * ARGCSR_EINVAL (see argcsr_last_error_message()) with no device work.
+ *
+ * Set-up: the first call on a device looks up the device address of the
+ * scratch array (cudaGetSymbolAddress) with that device current.  Make that
+ * first call before any stream capture on the device.
+ *
+ * Sharing: every call on a device uses the same scratch array, which keeps
+ * the previous call's contents (the parts that must start at zero are
+ * cleared by each call).  Calls whose work overlaps on the GPU -- on two
+ * streams, or from two host threads -- race on it: order them.
+ *
+ * Inputs are those of argcsr_create_from_csr.  Outputs, caller-owned device
+ * memory in the layout of argcsr_export:
+ *   d_groupInfo      int32[4 * group_capacity] ({firstRow, size, offset,
+ *                    chunkSize} per group, 16-byte aligned),
+ *   d_threadsMapping int32[n_rows] (always written),
+ *   d_out_columns    int32[slot_capacity],
+ *   d_out_values     slot_capacity elements of `dtype`.
+ * *h_n_groups and *h_n_slots receive the required sizes.  If a capacity is
+ * too small the call returns ARGCSR_EINVAL after setting them, writes no
+ * group records or slots, and can be repeated with larger buffers (pass 0
+ * capacities to query the sizes).  Synchronises `stream` like
+ * argcsr_create_from_csr.
+ * ------------------------------------------------------------------------ */
+#define ARGCSR_NOALLOC_MAX_ROWS 1048576
+#define ARGCSR_NOALLOC_SCRATCH_BYTES 17996032
+ARGCSR_API argcsr_status argcsr_convert_noalloc(
+    int32_t n_rows, int32_t n_cols, int64_t nnz,
+    const int32_t *d_rowPointers, const int32_t *d_columns, const void *d_values,
+    argcsr_dtype dtype, const argcsr_params *params,
+    int32_t *d_groupInfo, int64_t group_capacity, int32_t *d_threadsMapping,
+    int32_t *d_out_columns, void *d_out_values, int64_t slot_capacity,
+    int64_t *h_n_groups, int64_t *h_n_slots, argcsr_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * Baseline: SpMV straight on CSR (Section 2), for comparison only.
  *   variant 0: one thread per row (scalar CSR);
  *   variant 1: a group of 2..32 lanes per row, sized from the mean row

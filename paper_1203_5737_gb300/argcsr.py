@@ -67,6 +67,9 @@ _SIGNATURES = {
     "argcsr_launch_count": (_U64, []),
     "argcsr_trim_pool": (ctypes.c_int, []),
     "argcsr_version": (ctypes.c_char_p, []),
+    "argcsr_convert_noalloc": (ctypes.c_int, [_I32, _I32, _I64, _P, _P, _P, ctypes.c_int,
+                                              ctypes.POINTER(argcsr_params), _P, _I64, _P, _P, _P,
+                                              _I64, ctypes.POINTER(_I64), ctypes.POINTER(_I64), _P]),
     "argcsr_trace_begin": (ctypes.c_int, []),
     "argcsr_trace_end": (ctypes.c_int, []),
     "argcsr_trace_kernel_count": (ctypes.c_int32, []),
@@ -185,6 +188,21 @@ def argcsr_device_arrays(A):
 
 def argcsr_destroy(A, stream=0) -> None:
     _check(load_library().argcsr_destroy(A, stream), "argcsr_destroy")
+
+
+def argcsr_convert_noalloc(n_rows, n_cols, nnz, d_rowPointers, d_columns, d_values, dtype,
+                           group_size, desired_chunk_size, vec_width, d_groupInfo, group_capacity,
+                           d_threadsMapping, d_out_columns, d_out_values, slot_capacity, stream=0):
+    """The conversion into caller-owned buffers, allocating nothing.  Returns
+    (status, n_groups, n_slots) without raising, so a caller can size its
+    buffers from a first call with zero capacities."""
+    p = argcsr_params(group_size, desired_chunk_size, vec_width)
+    ng, ns = ctypes.c_int64(), ctypes.c_int64()
+    st = load_library().argcsr_convert_noalloc(
+        n_rows, n_cols, nnz, d_rowPointers, d_columns, d_values, dtype, ctypes.byref(p),
+        d_groupInfo, group_capacity, d_threadsMapping, d_out_columns, d_out_values, slot_capacity,
+        ctypes.byref(ng), ctypes.byref(ns), stream)
+    return st, ng.value, ns.value
 
 
 def argcsr_baseline_csr_spmv(n_rows, n_cols, nnz, d_rowPointers, d_columns, d_values, dtype,

@@ -18,6 +18,8 @@ argcsr_status record_cuda(cudaError_t err, const char *where) {
     return err == cudaErrorMemoryAllocation ? ARGCSR_ENOMEM : ARGCSR_ECUDA;
 }
 
+void set_error_message(const char *msg) { snprintf(t_last_error, sizeof t_last_error, "%s", msg); }
+
 // One pool per device, created on first use.  Its release threshold is
 // unbounded so that memory freed by one conversion is reused by the next
 // without returning to the driver; argcsr_trim_pool() gives it back.

@@ -35,6 +35,8 @@
 // "one thread remains free").
 #include <stdio.h>
 
+#include <mutex>
+
 #include "internal.cuh"
 
 namespace argcsr {
@@ -564,5 +566,142 @@ extern "C" ARGCSR_API argcsr_status argcsr_create_from_csr(
 
     A->device_bytes = (int64_t)A->n_groups * 16 + (int64_t)n * 4 + A->n_slots * (4 + (int64_t)es);
     *out = A;
+    return ARGCSR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// argcsr_convert_noalloc: the conversion with every intermediate array in one
+// file-scope device array, for callers that must not allocate device memory.
+// ---------------------------------------------------------------------------
+namespace argcsr {
+namespace {
+
+constexpr int kNoallocTile = 4096;                               // T for n <= 2^25
+constexpr int kNoallocMaxTiles = ARGCSR_NOALLOC_MAX_ROWS / kNoallocTile;
+constexpr size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+// carve-up of the scratch array (each part 256-byte aligned)
+constexpr size_t kOffDelta = 0;
+constexpr size_t kOffFn = kOffDelta + align256(ARGCSR_NOALLOC_MAX_ROWS);
+constexpr size_t kOffCnt = kOffFn + align256((size_t)kNoallocMaxTiles * 128);
+constexpr size_t kOffEntry = kOffCnt + align256((size_t)kNoallocMaxTiles * 128 * 4);
+constexpr size_t kOffGroupBase = kOffEntry + align256((size_t)kNoallocMaxTiles * 4);
+constexpr size_t kOffGroups = kOffGroupBase + align256((size_t)kNoallocMaxTiles * 4);
+constexpr size_t kOffTileSlots = kOffGroups + align256((size_t)ARGCSR_NOALLOC_MAX_ROWS * 16);
+constexpr size_t kOffTileSlotBase = kOffTileSlots + align256((size_t)kNoallocMaxTiles * 8);
+constexpr size_t kOffTotals = kOffTileSlotBase + align256((size_t)kNoallocMaxTiles * 8);
+constexpr size_t kNoallocBytes = kOffTotals + align256(sizeof(DeviceTotals));
+static_assert(ARGCSR_NOALLOC_MAX_ROWS % kNoallocTile == 0, "whole tiles");
+static_assert(kNoallocBytes == ARGCSR_NOALLOC_SCRATCH_BYTES, "header states the scratch size");
+
+// Every GPU that loads this library holds this array until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[64];
+
+// Device address of the scratch array on the current device, looked up once
+// per device.  The host-side name g_noalloc_scratch is not a device address.
+argcsr_status noalloc_scratch(unsigned char **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return record_cuda(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return ARGCSR_ENOTSUP;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return record_cuda(e, "cudaGetSymbolAddress(no-alloc scratch)");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = static_cast<unsigned char *>(g_noalloc_ptr[dev]);
+    return ARGCSR_OK;
+}
+
+}  // namespace
+}  // namespace argcsr
+
+extern "C" ARGCSR_API argcsr_status argcsr_convert_noalloc(
+    int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t *d_rowPointers,
+    const int32_t *d_columns, const void *d_values, argcsr_dtype dtype, const argcsr_params *params,
+    int32_t *d_groupInfo, int64_t group_capacity, int32_t *d_threadsMapping,
+    int32_t *d_out_columns, void *d_out_values, int64_t slot_capacity, int64_t *h_n_groups,
+    int64_t *h_n_slots, argcsr_stream_t stream) {
+    if (!h_n_groups || !h_n_slots) return ARGCSR_EINVAL;
+    *h_n_groups = 0;
+    *h_n_slots = 0;
+    if (!params || n_rows < 0 || n_cols < 0 || nnz < 0 || nnz > 0x7fffffffLL) return ARGCSR_EINVAL;
+    if (n_rows > ARGCSR_NOALLOC_MAX_ROWS) {
+        set_error_message("argcsr_convert_noalloc: n_rows exceeds ARGCSR_NOALLOC_MAX_ROWS");
+        return ARGCSR_EINVAL;
+    }
+    const int G = params->group_size, D = params->desired_chunk_size, V = params->vec_width;
+    if ((G != 32 && G != 64 && G != 128) || D < 1 || (V != 1 && V != 2 && V != 4)) return ARGCSR_EINVAL;
+    if (dtype != ARGCSR_F64 && dtype != ARGCSR_F32 && dtype != ARGCSR_BF16) return ARGCSR_EINVAL;
+    if (!d_rowPointers || (nnz > 0 && (!d_columns || !d_values))) return ARGCSR_EINVAL;
+    if (n_rows == 0) return nnz == 0 ? ARGCSR_OK : ARGCSR_EINVAL;
+    if (!d_threadsMapping || group_capacity < 0 || slot_capacity < 0) return ARGCSR_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_groupInfo) % 16) return ARGCSR_EINVAL;  // int4 records
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+
+    unsigned char *base = nullptr;
+    argcsr_status st = noalloc_scratch(&base);
+    if (st != ARGCSR_OK) return st;
+    uint8_t *delta = base + kOffDelta;
+    uint8_t *fn = base + kOffFn;
+    int *cnt = reinterpret_cast<int *>(base + kOffCnt);
+    int *tileEntry = reinterpret_cast<int *>(base + kOffEntry);
+    int *tileGroupBase = reinterpret_cast<int *>(base + kOffGroupBase);
+    int4 *gscratch = reinterpret_cast<int4 *>(base + kOffGroups);
+    long long *tileSlots = reinterpret_cast<long long *>(base + kOffTileSlots);
+    long long *tileSlotBase = reinterpret_cast<long long *>(base + kOffTileSlotBase);
+    DeviceTotals *tot = reinterpret_cast<DeviceTotals *>(base + kOffTotals);
+
+    const int n = n_rows, T = kNoallocTile;
+    const int numTiles = (n + T - 1) / T;
+    // the totals accumulate with atomics: they must start at zero every call
+    cudaError_t e = cudaMemsetAsync(tot, 0, sizeof(DeviceTotals), s);
+    if (e != cudaSuccess) return record_cuda(e, "cudaMemsetAsync");
+    {
+        TraceScope t("k_next_delta", s);
+        k_next_delta<<<(n + 255) / 256, 256, 0, s>>>(n, nnz, G, (long long)D * G, d_rowPointers, delta, tot);
+    }
+    count_launches(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return record_cuda(e, "k_next_delta");
+    switch (G) {
+        case 32: st = set_smem_limits<32>(T); if (!st) st = Kernels<32>::run_structure(n, T, numTiles, V, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
+        case 64: st = set_smem_limits<64>(T); if (!st) st = Kernels<64>::run_structure(n, T, numTiles, V, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
+        default: st = set_smem_limits<128>(T); if (!st) st = Kernels<128>::run_structure(n, T, numTiles, V, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
+    }
+    if (st != ARGCSR_OK) return st;
+    DeviceTotals h;
+    e = cudaMemcpyAsync(&h, tot, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return record_cuda(e, "argcsr_convert_noalloc: read totals");
+    if (h.status & kBadRowPointers) return ARGCSR_EINVAL;
+    if (h.status & kSlotOverflow) return ARGCSR_EOVERFLOW;
+    *h_n_groups = h.n_groups;
+    *h_n_slots = h.n_slots;
+    if (h.n_groups > group_capacity || h.n_slots > slot_capacity) {
+        set_error_message("argcsr_convert_noalloc: output capacity too small (required sizes returned)");
+        return ARGCSR_EINVAL;
+    }
+    if ((h.n_groups > 0 && !d_groupInfo) || (h.n_slots > 0 && (!d_out_columns || !d_out_values)))
+        return ARGCSR_EINVAL;
+    int4 *gi = reinterpret_cast<int4 *>(d_groupInfo);
+    const size_t es = dtype_size(dtype);
+#define FILL(GG, VT)                                                                              \
+    Kernels<GG>::template run_fill<VT>(h.n_groups, numTiles, V, n_cols, tileGroupBase, tileSlotBase, \
+                                       gscratch, d_rowPointers, d_columns, d_values,               \
+                                       d_threadsMapping, gi, d_out_columns, d_out_values, tot, s)
+    if (es == 8) st = G == 32 ? FILL(32, double) : G == 64 ? FILL(64, double) : FILL(128, double);
+    else if (es == 4) st = G == 32 ? FILL(32, float) : G == 64 ? FILL(64, float) : FILL(128, float);
+    else st = G == 32 ? FILL(32, uint16_t) : G == 64 ? FILL(64, uint16_t) : FILL(128, uint16_t);
+#undef FILL
+    if (st != ARGCSR_OK) return st;
+    e = cudaMemcpyAsync(&h, tot, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return record_cuda(e, "argcsr_convert_noalloc: read status");
+    if (h.status & kBadColumn) return ARGCSR_EINVAL;
     return ARGCSR_OK;
 }

@@ -62,6 +62,8 @@ struct TraceScope {
 // Record a CUDA error for argcsr_last_error_message(); returns ARGCSR_ECUDA
 // (or ARGCSR_ENOMEM for allocation failures).
 argcsr_status record_cuda(cudaError_t err, const char *where);
+// Set the text returned by argcsr_last_error_message() for a non-CUDA error.
+void set_error_message(const char *msg);
 
 // Stream-ordered allocation from the library's per-device pool.
 argcsr_status pool_alloc(void **p, size_t bytes, cudaStream_t s);

@@ -6,17 +6,19 @@
 // would become its (G+1)-th.  It is made parallel here without changing its
 // result:
 //   1. next[s] -- where a group that started at row s would end -- depends
-//      only on s, and next[s] - s is in [1, G] (k_next_delta, binary search
-//      in rowPointers);
+//      only on s, and next[s] - s is in [1, G] (binary search in a shared
+//      copy of rowPointers);
 //   2. the true group starts are the chain 0, next[0], next[next[0]], ...
 //      Rows are cut into tiles of T rows; since consecutive starts are at
 //      most G apart, the chain enters a tile at one of its first G rows.  Per
-//      tile and per possible entry, k_tile_walk follows the chain through the
-//      tile and records where it leaves and how many starts it met -- a
-//      function on G values;
+//      tile and per possible entry, k_tile_prepare (which also computes step
+//      1) finds where the chain leaves the tile and how many starts it meets
+//      -- a function on G values -- by composing the same functions of
+//      sub-tiles of 64 (or G) rows, whose short walks run in parallel;
 //   3. k_resolve composes those functions in tile order (one CTA), which
 //      gives every tile its true entry row and the index of its first group;
-//   4. k_groups walks each tile from its true entry, and for every group
+//   4. k_groups walks each tile from its true entry (sub-tile tables again,
+//      so the walk is S short parallel walks), and for every group
 //      computes the chunk size, the per-row thread counts and the group-local
 //      inclusive prefix (threadsMapping), and the group's slot offset inside
 //      the tile;
@@ -46,29 +48,6 @@ constexpr unsigned FULL = 0xffffffffu;
 
 __device__ __forceinline__ void flag(unsigned *status, unsigned bits) { atomicOr(status, bits); }
 
-// ---------------------------------------------------------------------------
-// 1. next[s] - s for every row s, and validation of rowPointers.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256)
-k_next_delta(int n, long long nnz, int G, long long limit, const int *__restrict__ rp,
-             uint8_t *__restrict__ delta, DeviceTotals *tot) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    const int a = rp[s], b = rp[s + 1];
-    if (b < a || (s == 0 && a != 0) || (s == n - 1 && (long long)b != nnz))
-        flag(&tot->status, kBadRowPointers);
-    // the group that starts at s ends after the first row r with
-    // rp[r+1] - rp[s] > limit, or at s + G, or at n
-    const int e = min(s + G, n);
-    int lo = s, hi = e;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if ((long long)rp[mid + 1] - a > limit) hi = mid; else lo = mid + 1;
-    }
-    const int next = lo < e ? lo + 1 : e;
-    delta[s] = (uint8_t)(next - s);
-}
-
 // Copy delta[base, base + lim) into shared memory with 16-byte loads.  The
 // delta buffer is padded to 256 bytes, so the rounded-up tail stays inside.
 __device__ __forceinline__ void load_tile_delta(uint8_t *d, const uint8_t *__restrict__ delta,
@@ -79,23 +58,83 @@ __device__ __forceinline__ void load_tile_delta(uint8_t *d, const uint8_t *__res
     for (int i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = src[i];
 }
 
+// Sub-tiles of B rows (B >= G) cut a tile's chain walk into short pieces.
+// For sub-tile s and entry e < G (the chain enters a sub-tile within its
+// first G rows), fnA[s*G+e] is where the chain from row s*B+e leaves the
+// sub-tile (offset past its end, < G) and cntA[s*G+e] how many group starts
+// it meets.  All S*G short walks run in parallel.
+template <int G>
+__device__ __forceinline__ void subtile_tables(const uint8_t *d, int lim, int B, int S,
+                                               uint8_t *fnA, uint8_t *cntA) {
+    for (int j = threadIdx.x; j < S * G; j += blockDim.x) {
+        const int sub = j / G, e = j - sub * G;
+        const int end = min((sub + 1) * B, lim);
+        int pos = sub * B + e, c = 0;
+        while (pos < end) { ++c; pos += d[pos]; }
+        fnA[j] = (uint8_t)min(max(pos - (sub + 1) * B, 0), G - 1);  // clamped past lim
+        cntA[j] = (uint8_t)c;
+    }
+}
+
+template <int G> constexpr int subtile_rows() { return G > 64 ? G : 64; }
+
+constexpr int kTileThreads = 512;   // threads of the per-tile kernels
+
 // ---------------------------------------------------------------------------
-// 2. Per tile and entry e < G: exit offset past the tile and starts met.
+// 1-2. Per tile: next[s] - s for every row s of the tile (and validation of
+// rowPointers), then, for every entry e < G, where the chain leaves the tile
+// and how many group starts it meets -- a function on G values.
 // ---------------------------------------------------------------------------
 template <int G>
-__global__ void __launch_bounds__(G)
-k_tile_walk(int n, int T, const uint8_t *__restrict__ delta, uint8_t *__restrict__ fn,
-            int *__restrict__ cnt) {
-    extern __shared__ __align__(16) uint8_t d[];
+__global__ void __launch_bounds__(kTileThreads)
+k_tile_prepare(int n, long long nnz, int T, long long limit, const int *__restrict__ rp,
+               uint8_t *__restrict__ delta, uint8_t *__restrict__ fn, int *__restrict__ cnt,
+               DeviceTotals *tot) {
+    constexpr int B = subtile_rows<G>();
+    const int S = T / B;
+    extern __shared__ __align__(16) uint8_t smem[];
+    int *s_rp = reinterpret_cast<int *>(smem);                         // T + G + 1
+    uint8_t *d = smem + 4 * ((size_t)T + G + 4);                        // T
+    uint8_t *fnA = d + T;                                               // S * G
+    uint8_t *cntA = fnA + (size_t)S * G;                                // S * G
     const int k = blockIdx.x;
-    const long long base = (long long)k * T;
-    const int lim = (int)min((long long)T, (long long)n - base);
-    load_tile_delta(d, delta, base, lim);
+    const long long tbase = (long long)k * T;
+    const int lim = (int)min((long long)T, (long long)n - tbase);
+    const int nrp = (int)min((long long)T + G + 1, (long long)n + 1 - tbase);
+#pragma unroll 4
+    for (int i = threadIdx.x; i < nrp; i += blockDim.x) s_rp[i] = rp[tbase + i];
     __syncthreads();
-    int pos = threadIdx.x, c = 0;
-    while (pos < lim) { ++c; pos += d[pos]; }
-    fn[(size_t)k * G + threadIdx.x] = lim == T ? (uint8_t)(pos - T) : (uint8_t)0;
-    cnt[(size_t)k * G + threadIdx.x] = c;
+    bool bad = false;
+    for (int i = threadIdx.x; i < lim; i += blockDim.x) {
+        const long long sr = tbase + i;
+        const int a = s_rp[i], b = s_rp[i + 1];
+        bad |= (b < a) | (sr == 0 && a != 0) | (sr == n - 1 && (long long)b != nnz);
+        // the group that starts at row sr ends after the first row r with
+        // rp[r+1] - rp[sr] > limit, or at sr + G, or at n
+        const int e = (int)min((long long)i + G, (long long)n - tbase);
+        int lo = i, hi = e;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if ((long long)s_rp[mid + 1] - a > limit) hi = mid; else lo = mid + 1;
+        }
+        const int next = lo < e ? lo + 1 : e;
+        d[i] = (uint8_t)(next - i);
+        delta[sr] = (uint8_t)(next - i);
+    }
+    if (bad) flag(&tot->status, kBadRowPointers);
+    __syncthreads();
+    subtile_tables<G>(d, lim, B, S, fnA, cntA);
+    __syncthreads();
+    // compose the sub-tile functions for every entry into the tile
+    for (int e = threadIdx.x; e < G; e += blockDim.x) {
+        int pos = e, c = 0;
+        for (int sub = 0; sub < S; ++sub) {
+            c += cntA[sub * G + pos];
+            pos = fnA[sub * G + pos];
+        }
+        fn[(size_t)k * G + e] = lim == T ? (uint8_t)pos : (uint8_t)0;
+        cnt[(size_t)k * G + e] = c;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -141,15 +180,23 @@ k_resolve(int numTiles, const uint8_t *__restrict__ fn, const int *__restrict__ 
     int pos[E], acc[E];
 #pragma unroll
     for (int q = 0; q < E; ++q) { pos[q] = lane + 32 * q; acc[q] = 0; }
-    for (int k = k0; k < k1; ++k) {
-        int f[E], c[E];
-        load_table<G>(k, lane, fn, cnt, f, c);
+    // the tables do not depend on the walk: load a batch of them at once
+    constexpr int P = 8 / E;
+    for (int kb = k0; kb < k1; kb += P) {
+        int f[P][E], c[P][E];
 #pragma unroll
-        for (int q = 0; q < E; ++q) {
-            int fp, cp;
-            lookup<G>(f, c, pos[q], fp, cp);
-            acc[q] += cp;
-            pos[q] = fp;
+        for (int u = 0; u < P; ++u)
+            if (kb + u < k1) load_table<G>(kb + u, lane, fn, cnt, f[u], c[u]);
+#pragma unroll
+        for (int u = 0; u < P; ++u) {
+            if (kb + u >= k1) break;
+#pragma unroll
+            for (int q = 0; q < E; ++q) {
+                int fp, cp;
+                lookup<G>(f[u], c[u], pos[q], fp, cp);
+                acc[q] += cp;
+                pos[q] = fp;
+            }
         }
     }
 #pragma unroll
@@ -168,122 +215,148 @@ k_resolve(int numTiles, const uint8_t *__restrict__ fn, const int *__restrict__ 
     }
     __syncthreads();
     int entry = segEntry[w], base = segBase[w];
-    for (int k = k0; k < k1; ++k) {
-        int f[E], c[E];
-        load_table<G>(k, lane, fn, cnt, f, c);
-        if (lane == 0) { tileEntry[k] = entry; tileGroupBase[k] = base; }
-        int fp, cp;
-        lookup<G>(f, c, entry, fp, cp);
-        base += cp;
-        entry = fp;
+    for (int kb = k0; kb < k1; kb += P) {
+        int f[P][E], c[P][E];
+#pragma unroll
+        for (int u = 0; u < P; ++u)
+            if (kb + u < k1) load_table<G>(kb + u, lane, fn, cnt, f[u], c[u]);
+#pragma unroll
+        for (int u = 0; u < P; ++u) {
+            if (kb + u >= k1) break;
+            if (lane == 0) { tileEntry[kb + u] = entry; tileGroupBase[kb + u] = base; }
+            int fp, cp;
+            lookup<G>(f[u], c[u], entry, fp, cp);
+            base += cp;
+            entry = fp;
+        }
     }
+}
+
+// ceil(l / d) for 0 <= l < 2^31 and 1 <= d < 2^31, given m = floor((2^32-1)/d):
+// q = umulhi(l, m) is at most 2 below floor(l / d), so two corrections make
+// it exact.  One hardware divide per divisor instead of one per row.
+__device__ __forceinline__ unsigned ceil_div_by(unsigned l, unsigned d, unsigned m) {
+    unsigned q = __umulhi(l, m);
+    unsigned r = l - q * d;
+    if (r >= d) { ++q; r -= d; }
+    if (r >= d) { ++q; r -= d; }
+    return q + (r != 0u);
 }
 
 // ---------------------------------------------------------------------------
 // 4. Groups of a tile: chunk size, threadsMapping, slot offset in the tile.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ long long warp_sum_ll(long long v) {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-    return v;
-}
-
 template <int G>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kTileThreads)
 k_groups(int n, int T, int V, const int *__restrict__ rp, const uint8_t *__restrict__ delta,
          const int *__restrict__ tileEntry, const int *__restrict__ tileGroupBase,
          int4 *__restrict__ gscratch, int *__restrict__ threadsMapping,
          long long *__restrict__ tileSlots, DeviceTotals *tot) {
-    constexpr int E = G / 32;
+    constexpr int B = subtile_rows<G>();
+    const int S = T / B;
     extern __shared__ __align__(16) uint8_t smem[];
-    uint8_t *d = smem;                                             // T bytes
-    uint16_t *starts = reinterpret_cast<uint16_t *>(smem + T);     // T entries
-    long long *slots = reinterpret_cast<long long *>(smem + 3 * (size_t)T);  // T entries
+    uint8_t *d = smem;                                              // T bytes
+    uint16_t *starts = reinterpret_cast<uint16_t *>(smem + T);      // T entries
+    int *chunk = reinterpret_cast<int *>(smem + 3 * (size_t)T);     // T entries
+    int *lens = reinterpret_cast<int *>(smem + 7 * (size_t)T);      // T + G entries
+    uint8_t *fnA = smem + 11 * (size_t)T + 4 * (size_t)G;           // S * G
+    uint8_t *cntA = fnA + (size_t)S * G;                            // S * G
+    uint16_t *subEntry = reinterpret_cast<uint16_t *>(cntA + (size_t)S * G);  // S
+    uint16_t *subBase = subEntry + S;                                         // S
     __shared__ int s_count;
-    __shared__ long long s_warp[8];
+    __shared__ long long s_warp[kTileThreads / 32];
 
     const int k = blockIdx.x;
     const long long tbase = (long long)k * T;
     const int lim = (int)min((long long)T, (long long)n - tbase);
+    // row lengths of the tile and of the G rows after it (a group that starts
+    // in the tile may end in the next); a decreasing rowPointers is flagged in
+    // k_tile_prepare, here it only has to stay bounded
+    const int nl = (int)min((long long)T + G, (long long)n - tbase);
+#pragma unroll 8
+    for (int i = threadIdx.x; i < nl; i += blockDim.x) {
+        const int a = rp[tbase + i], b = rp[tbase + i + 1];
+        lens[i] = b > a ? b - a : 0;
+    }
     load_tile_delta(d, delta, tbase, lim);
     __syncthreads();
+    // the chain through the tile from its true entry, in three parallel steps:
+    // per sub-tile tables, one pass over the S sub-tiles, per sub-tile walks
+    subtile_tables<G>(d, lim, B, S, fnA, cntA);
+    __syncthreads();
     if (threadIdx.x == 0) {
-        int pos = tileEntry[k], c = 0;
-        while (pos < lim) { starts[c++] = (uint16_t)pos; pos += d[pos]; }
-        s_count = c;
+        int entry = tileEntry[k], base = 0;
+        for (int sub = 0; sub < S; ++sub) {
+            subEntry[sub] = (uint16_t)entry;
+            subBase[sub] = (uint16_t)base;
+            base += cntA[sub * G + entry];
+            entry = fnA[sub * G + entry];
+        }
+        s_count = base;
+    }
+    __syncthreads();
+    for (int sub = threadIdx.x; sub < S; sub += blockDim.x) {
+        const int end = min((sub + 1) * B, lim);
+        int pos = sub * B + subEntry[sub], c = subBase[sub];
+        while (pos < end) { starts[c++] = (uint16_t)pos; pos += d[pos]; }
     }
     __syncthreads();
     const int count = s_count;
     const int gbase = tileGroupBase[k];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    for (int i = warp; i < count; i += 8) {
-        const int first = (int)(tbase + starts[i]);
-        const int size = d[starts[i]];
-        long long len[E];
-        long long nnz = 0, maxlen = 0;
-#pragma unroll
-        for (int q = 0; q < E; ++q) {
-            const int r = lane * E + q;
-            len[q] = 0;
-            if (r < size) {
-                const long long l = (long long)rp[first + r + 1] - rp[first + r];
-                len[q] = l > 0 ? l : 0;  // a decreasing rowPointers is flagged in k_next_delta
-            }
-            nnz += len[q];
-            maxlen = max(maxlen, len[q]);
+    // one thread per group: a tile holds hundreds of groups of <= G rows
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        const int start = starts[i];
+        const int size = d[start];
+        const int *L = lens + start;
+        unsigned maxlen = 0;
+        long long nnz = 0;
+        for (int r = 0; r < size; ++r) {
+            maxlen = max(maxlen, (unsigned)L[r]);
+            nnz += L[r];
         }
-        nnz = warp_sum_ll(nnz);
-#pragma unroll
-        for (int o = 16; o; o >>= 1) maxlen = max(maxlen, __shfl_xor_sync(FULL, maxlen, o));
         long long C = 0;
         if (maxlen > 0) {
-            long long lo = max(1LL, (nnz + G - 1) / G), hi = maxlen;
+            // C >= nnz / G (all threads busy) and C >= maxlen / (G - size + 1)
+            // (the longest row gets at most the spare threads plus its own)
+            unsigned lo = (unsigned)max((nnz + G - 1) / G,
+                                        (long long)((maxlen + (G - size)) / (G - size + 1)));
+            unsigned hi = maxlen;
+            lo = max(lo, 1u);
             while (lo < hi) {
-                const long long mid = lo + ((hi - lo) >> 1);
-                long long need = 0;
-#pragma unroll
-                for (int q = 0; q < E; ++q)
-                    if (lane * E + q < size) need += max(1LL, (len[q] + mid - 1) / mid);
-                need = warp_sum_ll(need);
+                const unsigned mid = lo + ((hi - lo) >> 1);
+                const unsigned m = 0xffffffffu / mid;
+                int need = 0;
+                for (int r = 0; r < size && need <= G; ++r) {
+                    const unsigned l = (unsigned)L[r];
+                    need += l > mid ? (int)ceil_div_by(l, mid, m) : 1;
+                }
                 if (need <= G) hi = mid; else lo = mid + 1;
             }
-            C = (lo + V - 1) / V * V;
+            C = ((long long)lo + V - 1) / V * V;
         }
-        // thread counts and the group-local inclusive prefix
-        int t[E], local = 0;
-#pragma unroll
-        for (int q = 0; q < E; ++q) {
-            t[q] = 0;
-            if (lane * E + q < size) t[q] = C == 0 ? 1 : (int)max(1LL, (len[q] + C - 1) / C);
-            local += t[q];
+        // thread counts and the group-local inclusive prefix (threadsMapping)
+        int prefix = 0;
+        const int first = (int)(tbase + start);
+        const unsigned Cu = C > 0 && C <= 0x7fffffffLL ? (unsigned)C : 0u;
+        const unsigned Cm = Cu ? 0xffffffffu / Cu : 0u;
+        for (int r = 0; r < size; ++r) {
+            const unsigned l = (unsigned)L[r];
+            prefix += (Cu == 0u || l <= Cu) ? 1 : (int)ceil_div_by(l, Cu, Cm);
+            threadsMapping[first + r] = prefix;
         }
-        int incl = local;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(FULL, incl, o);
-            if (lane >= o) incl += v;
-        }
-        int prefix = incl - local;
-#pragma unroll
-        for (int q = 0; q < E; ++q) {
-            if (lane * E + q < size) {
-                prefix += t[q];
-                threadsMapping[first + lane * E + q] = prefix;
-            }
-        }
-        if (lane == 0) {
-            gscratch[gbase + i] = make_int4(first, size, 0, C <= 0x7fffffffLL ? (int)C : -1);
-            slots[i] = C * G;
-            if (C > 0x7fffffffLL) flag(&tot->status, kSlotOverflow);
-        }
+        // the record keeps the tile index beside the size (size <= 128)
+        gscratch[gbase + i] = make_int4(first, size | (k << 8), 0, C <= 0x7fffffffLL ? (int)C : -1);
+        chunk[i] = C <= 0x7fffffffLL ? (int)C : 0x7fffffff;
+        if (C > 0x7fffffffLL) flag(&tot->status, kSlotOverflow);
     }
     __syncthreads();
-    // exclusive scan of slots[0, count) -> slot offset of each group in the tile
-    const int per = (count + 255) / 256;
+    // exclusive scan of chunk[i] * G -> slot offset of each group in the tile
+    const int per = (count + kTileThreads - 1) / kTileThreads;
     const int i0 = min(count, (int)threadIdx.x * per), i1 = min(count, i0 + per);
     long long mine = 0;
-    for (int i = i0; i < i1; ++i) mine += slots[i];
+    for (int i = i0; i < i1; ++i) mine += (long long)chunk[i] * G;
     long long incl = mine;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -298,11 +371,11 @@ k_groups(int n, int T, int V, const int *__restrict__ rp, const uint8_t *__restr
     for (int i = i0; i < i1; ++i) {
         if (run > 0x7fffffffLL) flag(&tot->status, kSlotOverflow);
         gscratch[gbase + i].z = (int)min(run, 0x7fffffffLL);
-        run += slots[i];
+        run += (long long)chunk[i] * G;
     }
-    if (threadIdx.x == 255) {
+    if (threadIdx.x == kTileThreads - 1) {
         long long total = 0;
-        for (int v = 0; v < 8; ++v) total += s_warp[v];
+        for (int v = 0; v < kTileThreads / 32; ++v) total += s_warp[v];
         tileSlots[k] = total;
     }
 }
@@ -344,74 +417,115 @@ k_tile_scan(int numTiles, const long long *__restrict__ tileSlots, long long *__
 // ---------------------------------------------------------------------------
 template <int G, typename VT>
 __global__ void __launch_bounds__(256)
-k_fill(long long nGroups, int numTiles, int V, int n_cols, const int *__restrict__ tileGroupBase,
-       const long long *__restrict__ tileSlotBase, const int4 *__restrict__ gscratch,
-       const int *__restrict__ rp, const int *__restrict__ colsIn, const VT *__restrict__ valsIn,
-       const int *__restrict__ threadsMapping, int4 *__restrict__ groupInfo,
-       int *__restrict__ colsOut, VT *__restrict__ valsOut, DeviceTotals *tot) {
-    const int lane = threadIdx.x & 31;
+k_fill(long long nGroups, int V, int n_cols, const long long *__restrict__ tileSlotBase,
+       const int4 *__restrict__ gscratch, const int *__restrict__ rp, const int *__restrict__ colsIn,
+       const VT *__restrict__ valsIn, const int *__restrict__ threadsMapping,
+       int4 *__restrict__ groupInfo, int *__restrict__ colsOut, VT *__restrict__ valsOut,
+       DeviceTotals *tot) {
+    __shared__ short s_rowOf[8][G];     // chunk -> row of the group (G > 32)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
     bool bad = false;
-    for (long long g = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < nGroups;
-         g += warps) {
+    for (long long g = (long long)blockIdx.x * (blockDim.x >> 5) + warp; g < nGroups; g += warps) {
         const int4 s = gscratch[g];
-        // tile of g: the last tile whose first group index is <= g
-        int lo = 0, hi = numTiles - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (tileGroupBase[mid] <= g) lo = mid; else hi = mid - 1;
-        }
-        const long long off = tileSlotBase[lo] + s.z;
-        const int first = s.x, size = s.y, C = s.w;
+        const int first = s.x, size = s.y & 255, C = s.w;
+        const long long off = tileSlotBase[s.y >> 8] + s.z;
         if (lane == 0) groupInfo[g] = make_int4(first, size, (int)off, C);
         if (C <= 0) continue;
+        if constexpr (G > 32) {
+            for (int c = lane; c < G; c += 32) s_rowOf[warp][c] = -1;
+            __syncwarp();
+            for (int r = lane; r < size; r += 32) {
+                const int b = r ? threadsMapping[first + r - 1] : 0, e = threadsMapping[first + r];
+                for (int c = b; c < e; ++c) s_rowOf[warp][c] = (short)r;
+            }
+            __syncwarp();
+        }
 #pragma unroll
         for (int q = 0; q < G / 32; ++q) {
             const int c = q * 32 + lane;
-            // row of chunk c: the first row whose inclusive prefix exceeds c
-            int a = 0, b = size;
-            while (a < b) {
-                const int mid = (a + b) >> 1;
-                if (threadsMapping[first + mid] > c) b = mid; else a = mid + 1;
+            int row, begin;
+            if constexpr (G == 32) {
+                // row ends as a bit mask: the row of chunk c is the number of
+                // ends below c, its first chunk follows the previous end
+                const int end = lane < size ? threadsMapping[first + lane] : 0;
+                const unsigned ends = __reduce_or_sync(FULL, lane < size ? 1u << (end - 1) : 0u);
+                const unsigned below = ends & ((1u << lane) - 1u);
+                row = __popc(below);
+                begin = below ? 32 - __clz(below) : 0;
+            } else {
+                row = s_rowOf[warp][c];
+                if (row < 0) row = size;
+                begin = (row > 0 && row < size) ? threadsMapping[first + row - 1] : 0;
             }
-            long long src = 0, fill = 0;
-            if (a < size) {
-                const int r = first + a;
-                const int begin = a == 0 ? 0 : threadsMapping[r - 1];
-                const long long kk = c - begin;
-                const long long len = (long long)rp[r + 1] - rp[r];
-                src = rp[r] + kk * C;
-                fill = min((long long)C, max(0LL, len - kk * C));
+            long long src = 0;
+            int fill = 0;
+            if (row < size) {
+                const int r = first + row;
+                const int rs = rp[r];
+                const long long kk = (long long)(c - begin) * C;
+                const long long len = (long long)rp[r + 1] - rs;
+                src = rs + kk;
+                fill = (int)min((long long)C, max(0LL, len - kk));
             }
-            for (int j = 0; j < C; ++j) {
-                const long long slot = off + (long long)(j / V) * G * V + (long long)c * V + (j % V);
-                int col = -1;
-                VT val;
-                memset(&val, 0, sizeof val);
-                if (j < fill) {
-                    col = colsIn[src + j];
-                    val = valsIn[src + j];
-                    bad |= (col < 0) | (col >= n_cols);
+            // a chunk's elements are contiguous in the CSR arrays; lanes of one
+            // row read C apart, which L1 serves from the lines already fetched
+            for (int j0 = 0; j0 < C; j0 += 4) {
+                int cc[4];
+                VT vv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = j0 + u;
+                    cc[u] = -1;
+                    memset(&vv[u], 0, sizeof(VT));
+                    if (j < fill) {
+                        cc[u] = colsIn[src + j];
+                        vv[u] = valsIn[src + j];
+                        bad |= (cc[u] < 0) | (cc[u] >= n_cols);
+                    }
                 }
-                colsOut[slot] = col;
-                valsOut[slot] = val;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = j0 + u;
+                    if (j < C) {
+                        const long long slot = off + (long long)(j / V) * G * V + (long long)c * V + (j % V);
+                        colsOut[slot] = cc[u];
+                        valsOut[slot] = vv[u];
+                    }
+                }
             }
         }
+        if constexpr (G > 32) __syncwarp();
     }
     if (__any_sync(FULL, bad) && lane == 0) flag(&tot->status, kBadColumn);
+}
+
+// Dynamic shared memory of k_groups: delta (T), starts (2T), chunk sizes
+// (4T), row lengths (4(T+G)), sub-tile tables (2 S G), sub-tile entries and
+// bases (4 S).
+inline size_t groups_smem(int T, int G) {
+    const int S = T / (G > 64 ? G : 64);
+    return (size_t)T * 11 + 4 * (size_t)G + 2 * (size_t)S * G + 4 * (size_t)S;
+}
+// Dynamic shared memory of k_tile_prepare: rowPointers (4(T+G+4)), delta
+// (T), sub-tile tables (2 S G).
+inline size_t prepare_smem(int T, int G) {
+    const int S = T / (G > 64 ? G : 64);
+    return 4 * ((size_t)T + G + 4) + (size_t)T + 2 * (size_t)S * G;
 }
 
 // Kernels for one group size.
 template <int G>
 struct Kernels {
-    static argcsr_status run_structure(int n, int T, int numTiles, int V, const int *rp,
-                                       const uint8_t *delta, uint8_t *fn, int *cnt, int *tileEntry,
-                                       int *tileGroupBase, int4 *gscratch, int *tm,
+    static argcsr_status run_structure(int n, long long nnz, long long limit, int T, int numTiles,
+                                       int V, const int *rp, uint8_t *delta, uint8_t *fn, int *cnt,
+                                       int *tileEntry, int *tileGroupBase, int4 *gscratch, int *tm,
                                        long long *tileSlots, long long *tileSlotBase,
                                        DeviceTotals *tot, cudaStream_t s) {
         {
-            TraceScope t("k_tile_walk", s);
-            k_tile_walk<G><<<numTiles, G, T, s>>>(n, T, delta, fn, cnt);
+            TraceScope t("k_tile_prepare", s);
+            k_tile_prepare<G><<<numTiles, kTileThreads, prepare_smem(T, G), s>>>(n, nnz, T, limit, rp, delta,
+                                                                       fn, cnt, tot);
         }
         {
             TraceScope t("k_resolve", s);
@@ -419,8 +533,8 @@ struct Kernels {
         }
         {
             TraceScope t("k_groups", s);
-            const size_t smem = (size_t)T * 11;  // delta, starts (u16), slots (i64)
-            k_groups<G><<<numTiles, 256, smem, s>>>(n, T, V, rp, delta, tileEntry, tileGroupBase,
+            const size_t smem = groups_smem(T, G);
+            k_groups<G><<<numTiles, kTileThreads, smem, s>>>(n, T, V, rp, delta, tileEntry, tileGroupBase,
                                                      gscratch, tm, tileSlots, tot);
         }
         {
@@ -432,8 +546,8 @@ struct Kernels {
         return ARGCSR_OK;
     }
     template <typename VT>
-    static argcsr_status run_fill(long long nGroups, int numTiles, int V, int n_cols,
-                                  const int *tileGroupBase, const long long *tileSlotBase,
+    static argcsr_status run_fill(long long nGroups, int V, int n_cols,
+                                  const long long *tileSlotBase,
                                   const int4 *gscratch, const int *rp, const int *cols,
                                   const void *vals, const int *tm, int4 *gi, int *colsOut,
                                   void *valsOut, DeviceTotals *tot, cudaStream_t s) {
@@ -441,7 +555,7 @@ struct Kernels {
         const long long blocks = min((nGroups + 7) / 8, 152LL * 64);
         TraceScope t("k_fill", s);
         k_fill<G, VT><<<(unsigned)blocks, 256, 0, s>>>(
-            nGroups, numTiles, V, n_cols, tileGroupBase, tileSlotBase, gscratch, rp, cols,
+            nGroups, V, n_cols, tileSlotBase, gscratch, rp, cols,
             static_cast<const VT *>(vals), tm, gi, colsOut, static_cast<VT *>(valsOut), tot);
         count_launches(1);
         ARGCSR_CHECK_LAUNCH("k_fill");
@@ -451,10 +565,12 @@ struct Kernels {
 
 template <int G>
 argcsr_status set_smem_limits(int T) {
-    const size_t smem = (size_t)T * 11;
     cudaError_t e = cudaFuncSetAttribute(k_groups<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return record_cuda(e, "cudaFuncSetAttribute(k_groups)");
+                                         (int)groups_smem(T, G));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_tile_prepare<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)prepare_smem(T, G));
+    if (e != cudaSuccess) return record_cuda(e, "cudaFuncSetAttribute");
     return ARGCSR_OK;
 }
 
@@ -491,7 +607,9 @@ extern "C" ARGCSR_API argcsr_status argcsr_create_from_csr(
     if (n_rows == 0) { *out = A; return ARGCSR_OK; }
 
     const int n = n_rows;
-    const int T = n <= (1 << 25) ? 4096 : 16384;
+    // tiles of 2048 rows give a 2M-row matrix about 1000 per-tile blocks;
+    // very large matrices use longer tiles to keep k_resolve's table short
+    const int T = n <= (1 << 25) ? 2048 : 16384;
     const int numTiles = (int)(((long long)n + T - 1) / T);
     const size_t es = dtype_size(dtype);
 
@@ -520,19 +638,11 @@ extern "C" ARGCSR_API argcsr_status argcsr_create_from_csr(
 
     cudaError_t e = cudaMemsetAsync(tot, 0, sizeof(DeviceTotals), s);
     if (e != cudaSuccess) return fail(record_cuda(e, "cudaMemsetAsync"));
-    {
-        TraceScope t("k_next_delta", s);
-        k_next_delta<<<(n + 255) / 256, 256, 0, s>>>(n, nnz, G, (long long)D * G, d_rowPointers, delta, tot);
-    }
-    count_launches(1);
-    {
-        cudaError_t le = cudaGetLastError();
-        if (le != cudaSuccess) return fail(record_cuda(le, "k_next_delta"));
-    }
+    const long long limit = (long long)D * G;
     switch (G) {
-        case 32: st = set_smem_limits<32>(T); if (!st) st = Kernels<32>::run_structure(n, T, numTiles, V, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, A->d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
-        case 64: st = set_smem_limits<64>(T); if (!st) st = Kernels<64>::run_structure(n, T, numTiles, V, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, A->d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
-        default: st = set_smem_limits<128>(T); if (!st) st = Kernels<128>::run_structure(n, T, numTiles, V, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, A->d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
+        case 32: st = set_smem_limits<32>(T); if (!st) st = Kernels<32>::run_structure(n, nnz, limit, T, numTiles, V, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, A->d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
+        case 64: st = set_smem_limits<64>(T); if (!st) st = Kernels<64>::run_structure(n, nnz, limit, T, numTiles, V, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, A->d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
+        default: st = set_smem_limits<128>(T); if (!st) st = Kernels<128>::run_structure(n, nnz, limit, T, numTiles, V, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, A->d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
     }
     if (st != ARGCSR_OK) return fail(st);
 
@@ -550,7 +660,7 @@ extern "C" ARGCSR_API argcsr_status argcsr_create_from_csr(
     if ((st = pool_alloc(&A->d_values, (size_t)A->n_slots * es, s)) != ARGCSR_OK) return fail(st);
 
 #define FILL(GG, VT)                                                                             \
-    Kernels<GG>::template run_fill<VT>(A->n_groups, numTiles, V, n_cols, tileGroupBase, tileSlotBase, \
+    Kernels<GG>::template run_fill<VT>(A->n_groups, V, n_cols, tileSlotBase,                       \
                                        gscratch, d_rowPointers, d_columns, d_values,              \
                                        A->d_threadsMapping, A->d_groupInfo, A->d_columns,         \
                                        A->d_values, tot, s)
@@ -661,17 +771,11 @@ extern "C" ARGCSR_API argcsr_status argcsr_convert_noalloc(
     // the totals accumulate with atomics: they must start at zero every call
     cudaError_t e = cudaMemsetAsync(tot, 0, sizeof(DeviceTotals), s);
     if (e != cudaSuccess) return record_cuda(e, "cudaMemsetAsync");
-    {
-        TraceScope t("k_next_delta", s);
-        k_next_delta<<<(n + 255) / 256, 256, 0, s>>>(n, nnz, G, (long long)D * G, d_rowPointers, delta, tot);
-    }
-    count_launches(1);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return record_cuda(e, "k_next_delta");
+    const long long limit = (long long)D * G;
     switch (G) {
-        case 32: st = set_smem_limits<32>(T); if (!st) st = Kernels<32>::run_structure(n, T, numTiles, V, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
-        case 64: st = set_smem_limits<64>(T); if (!st) st = Kernels<64>::run_structure(n, T, numTiles, V, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
-        default: st = set_smem_limits<128>(T); if (!st) st = Kernels<128>::run_structure(n, T, numTiles, V, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
+        case 32: st = set_smem_limits<32>(T); if (!st) st = Kernels<32>::run_structure(n, nnz, limit, T, numTiles, V, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
+        case 64: st = set_smem_limits<64>(T); if (!st) st = Kernels<64>::run_structure(n, nnz, limit, T, numTiles, V, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
+        default: st = set_smem_limits<128>(T); if (!st) st = Kernels<128>::run_structure(n, nnz, limit, T, numTiles, V, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
     }
     if (st != ARGCSR_OK) return st;
     DeviceTotals h;
@@ -691,7 +795,7 @@ extern "C" ARGCSR_API argcsr_status argcsr_convert_noalloc(
     int4 *gi = reinterpret_cast<int4 *>(d_groupInfo);
     const size_t es = dtype_size(dtype);
 #define FILL(GG, VT)                                                                              \
-    Kernels<GG>::template run_fill<VT>(h.n_groups, numTiles, V, n_cols, tileGroupBase, tileSlotBase, \
+    Kernels<GG>::template run_fill<VT>(h.n_groups, V, n_cols, tileSlotBase,                        \
                                        gscratch, d_rowPointers, d_columns, d_values,               \
                                        d_threadsMapping, gi, d_out_columns, d_out_values, tot, s)
     if (es == 8) st = G == 32 ? FILL(32, double) : G == 64 ? FILL(64, double) : FILL(128, double);

@@ -11,15 +11,18 @@
 //    group record is one 16-byte load; the row of each chunk comes from a
 //    bit mask of row ends built with one warp reduction over threadsMapping
 //    (no shared memory, no block barrier); partial sums are combined with a
-//    segmented shuffle scan and the last lane of each row stores y.
+//    segmented shuffle reduction and the first lane of each row stores y.
 //  * G = 64 / 128: one group per G threads, the paper's shared-memory
 //    reduction (a row's owner thread adds its chunks' partials).
 //  * values/columns are streamed with evict-first loads (each slot is read
 //    once); x is gathered through the read-only path so that its lines stay
 //    in L2; V > 1 turns the per-thread loads into 8/16-byte vector loads.
-//  * the loop over a chunk runs in batches of four elements; a batch whose
-//    last element is padding in every lane of the warp ends the loop (the
-//    paper's early exit when a whole warp reaches artificial zeros).
+//  * the loop over a chunk runs in batches of four elements, the next batch
+//    loaded before the current one is consumed; the first batch is issued
+//    together with the threadsMapping load.  Padding is skipped per slot
+//    (column -1) rather than by a whole-warp exit: with the minimal chunk
+//    size some chunk of every group is full, so a warp never runs out of
+//    work before the last element row.
 #include "internal.cuh"
 
 namespace argcsr {
@@ -60,48 +63,89 @@ __device__ __forceinline__ void ld_stream(const T *p, T (&out)[V]) {
     }
 }
 
+#ifndef ARGCSR_SPMV_ELEMS
+#define ARGCSR_SPMV_ELEMS 4      // elements per lane per batch
+#endif
+#ifndef ARGCSR_SPMV_PREFETCH
+#define ARGCSR_SPMV_PREFETCH 1   // issue batch b+1 before consuming batch b
+#endif
+
+// One batch: U blocks of V consecutive elements of this lane's chunk.
+template <typename VT, int V, int U>
+struct Batch {
+    int c[U][V];
+    VT v[U][V];
+};
+
+// Load blocks [b, b+U) of a chunk (block b at base + b*stride).  Blocks past
+// nb, or every block when `on` is false, read as padding without a load.
+// Columns and values are loaded together: a value load does not wait for
+// its column.
+template <typename VT, int V, int U>
+__device__ __forceinline__ void load_batch(Batch<VT, V, U> &B, const int *__restrict__ cp,
+                                           const VT *__restrict__ vp, long long stride, int b,
+                                           int nb, bool on) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        if (on && b + u < nb) {
+            ld_stream<int, V>(cp + (long long)(b + u) * stride, B.c[u]);
+            ld_stream<VT, V>(vp + (long long)(b + u) * stride, B.v[u]);
+        } else {
+#pragma unroll
+            for (int e = 0; e < V; ++e) { B.c[u][e] = -1; B.v[u][e] = VT(0); }
+        }
+    }
+}
+
+// sum += v on lanes where `on` holds.  Written as a predicated PTX add so
+// that lanes without work issue no FP64 operation (a plain conditional add
+// may be turned into an add on every lane followed by a select).
+__device__ __forceinline__ void add_if(double &sum, double v, bool on) {
+    asm("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p add.rn.f64 %0, %0, %1;\n\t}"
+        : "+d"(sum) : "d"(v), "r"((unsigned)on));
+}
+__device__ __forceinline__ void add_if(float &sum, float v, bool on) {
+    if (on) sum += v;
+}
+
+template <typename VT, int V, int U>
+__device__ __forceinline__ void consume(const Batch<VT, V, U> &B,
+                                        const typename AccOf<VT>::type *__restrict__ x,
+                                        typename AccOf<VT>::type &sum) {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int e = 0; e < V; ++e)
+            if (B.c[u][e] >= 0) sum = fma(widen(B.v[u][e]), __ldg(x + B.c[u][e]), sum);
+}
+
 // Sum of one chunk: C/V blocks of V elements; block b of chunk c starts at
-// base + b*G*V + c*V.  Lanes that own no row (free chunks) load nothing.
-// Every lane of the warp must call this (it votes on early exit).
+// base + b*G*V + c*V.  The first batch may already be loaded (`first`); the
+// rest are loaded only by lanes that own a row.  A minimal chunk size leaves
+// at least one chunk of the group full, so the loop runs all C/V blocks (the
+// paper's whole-warp early exit at padding would never fire).
 template <int G, typename VT, int V>
 __device__ __forceinline__ typename AccOf<VT>::type
 chunk_sum(const int *__restrict__ cols, const VT *__restrict__ vals,
-          const typename AccOf<VT>::type *__restrict__ x, long long base, int C, bool owns) {
+          const typename AccOf<VT>::type *__restrict__ x, long long base, int C, bool owns,
+          Batch<VT, V, (ARGCSR_SPMV_ELEMS + V - 1) / V> &B) {
     using Acc = typename AccOf<VT>::type;
-    constexpr int U = V >= 4 ? 1 : 4 / V;   // blocks per batch: 4 elements
+    constexpr int U = (ARGCSR_SPMV_ELEMS + V - 1) / V;
     Acc sum = 0;
     const int nb = C / V;
     const int *cp = cols + base;
     const VT *vp = vals + base;
+    const long long stride = (long long)G * V;
     for (int b = 0; b < nb; b += U) {
-        int c[U][V];
-        VT v[U][V];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (owns && b + u < nb) {
-                ld_stream<int, V>(cp + (long long)(b + u) * G * V, c[u]);
-            } else {
-#pragma unroll
-                for (int e = 0; e < V; ++e) c[u][e] = -1;
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (c[u][0] >= 0) {
-                ld_stream<VT, V>(vp + (long long)(b + u) * G * V, v[u]);
-            } else {
-#pragma unroll
-                for (int e = 0; e < V; ++e) v[u][e] = VT(0);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-#pragma unroll
-            for (int e = 0; e < V; ++e) {
-                if (c[u][e] >= 0) sum = fma(widen(v[u][e]), __ldg(x + c[u][e]), sum);
-            }
-        }
-        if (__all_sync(FULL, c[U - 1][V - 1] < 0)) break;
+#if ARGCSR_SPMV_PREFETCH
+        Batch<VT, V, U> N;
+        load_batch<VT, V, U>(N, cp, vp, stride, b + U, nb, owns);
+        consume<VT, V, U>(B, x, sum);
+        B = N;
+#else
+        consume<VT, V, U>(B, x, sum);
+        load_batch<VT, V, U>(B, cp, vp, stride, b + U, nb, owns);
+#endif
     }
     return sum;
 }
@@ -113,26 +157,37 @@ k_spmv_g32(long long nGroups, const int4 *__restrict__ gi, const int *__restrict
            const int *__restrict__ cols, const VT *__restrict__ vals,
            const typename AccOf<VT>::type *__restrict__ x, typename AccOf<VT>::type *__restrict__ y) {
     using Acc = typename AccOf<VT>::type;
+    constexpr int U = (ARGCSR_SPMV_ELEMS + V - 1) / V;
     const int lane = threadIdx.x & 31;
     const long long g = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (g >= nGroups) return;  // warp-uniform
     const int4 info = __ldg(gi + g);  // firstRow, size, offset, chunkSize
     const int first = info.x, size = info.y, C = info.w;
+    const long long base = (long long)info.z + lane * V;
+    // the first batch does not depend on threadsMapping: issue it together
+    Batch<VT, V, U> B;
+    load_batch<VT, V, U>(B, cols + base, vals + base, 32LL * V, 0, C / V, true);
     const int end = lane < size ? __ldg(tm + first + lane) : 0;
     // bit k set <=> chunk k is the last chunk of a row
     const unsigned ends = __reduce_or_sync(FULL, lane < size ? 1u << (end - 1) : 0u);
     const unsigned below = ends & ((1u << lane) - 1u);
     const int row = __popc(below);          // local row of this lane's chunk
     const bool owns = row < size;           // false for free chunks
-    Acc sum = chunk_sum<32, VT, V>(cols, vals, x, (long long)info.z + lane * V, C, owns);
-    // segmented inclusive scan: add partials of lanes of the same row
+    Acc sum = chunk_sum<32, VT, V>(cols, vals, x, base, C, owns, B);
+    // Segmented tree reduction of the partial sums into the first lane of
+    // each row: a row of t chunks costs t - 1 FP64 adds (FP64 throughput on
+    // GB300 is about 2 operations per clock per SM, the same budget the FMAs
+    // use), in ceil(log2(longest row's chunk count)) steps -- none when every
+    // row of the group has a single chunk.
     const int segStart = below ? 32 - __clz(below) : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const Acc v = __shfl_up_sync(FULL, sum, o);
-        if (lane - o >= segStart) sum += v;
+    const unsigned atOrAbove = ends & ~((1u << lane) - 1u);
+    const int segEnd = atOrAbove ? __ffs(atOrAbove) : 0;   // one past the row's last chunk
+    const int maxChunks = __reduce_max_sync(FULL, owns ? segEnd - segStart : 0);
+    for (int o = 1; o < maxChunks; o <<= 1) {
+        const Acc v = __shfl_down_sync(FULL, sum, o);
+        add_if(sum, v, ((lane - segStart) & (2 * o - 1)) == 0 && lane + o < segEnd);
     }
-    if (owns && ((ends >> lane) & 1u)) y[first + row] = sum;
+    if (owns && lane == segStart) y[first + row] = sum;
 }
 
 // G = 64 or 128: one group per G threads, 256 / G groups per block.
@@ -160,12 +215,15 @@ k_spmv_block(long long nGroups, const int4 *__restrict__ gi, const int *__restri
     }
     __syncthreads();
     const bool owns = rowOf[threadIdx.x] >= 0;
-    // warps never straddle groups (G is a multiple of 32), so C is warp-uniform
-    partial[threadIdx.x] = chunk_sum<G, VT, V>(cols, vals, x, (long long)info.z + c * V, C, owns);
+    constexpr int U = (ARGCSR_SPMV_ELEMS + V - 1) / V;
+    const long long base = (long long)info.z + c * V;
+    Batch<VT, V, U> B;
+    load_batch<VT, V, U>(B, cols + base, vals + base, (long long)G * V, 0, C / V, owns);
+    partial[threadIdx.x] = chunk_sum<G, VT, V>(cols, vals, x, base, C, owns, B);
     __syncthreads();
     if (c < size) {
-        Acc s = 0;
-        for (int k = begin; k < end; ++k) s += partial[sub * G + k];
+        Acc s = partial[sub * G + begin];
+        for (int k = begin + 1; k < end; ++k) s += partial[sub * G + k];
         y[first + c] = s;
     }
 }

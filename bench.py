@@ -532,6 +532,37 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_ncu_case(which):
+    """A short, untimed launch sequence for ncu captures: for each matrix, one
+    conversion (k_tile_prepare, k_resolve, k_groups, k_tile_scan, k_fill) and
+    two SpMVs.  'bench' uses the bench's two matrices; 'small' a 1,000,000-row
+    lognormal matrix (D 4) and the 128^3 Laplacian (D 8) -- larger than L2,
+    about 1 GB on the device."""
+    import torch
+    from paper_1203_5737_gb300 import argcsr as api
+    from paper_1203_5737_gb300 import build
+    build.build()
+    s = torch.cuda.current_stream().cuda_stream
+    if which == "bench":
+        mats = [(synth.workload(name)[0], D) for name, D in MATRICES]
+    else:
+        mats = [(synth.laplacian_3d(128), 8), (synth.lognormal_rows(1_000_000), 4)]
+    for A, D in mats:
+        rp = torch.from_numpy(A.rowPointers).cuda()
+        cols = torch.from_numpy(A.columns).cuda()
+        vals = torch.from_numpy(A.values).cuda()
+        x = torch.rand(A.n_cols, dtype=torch.float64, device="cuda")
+        y = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
+        h = api.argcsr_create_from_csr(A.n_rows, A.n_cols, A.nnz, rp.data_ptr(), cols.data_ptr(),
+                                       vals.data_ptr(), api.ARGCSR_F64, GROUP_SIZE, D, 1, s)
+        for _ in range(2):
+            api.argcsr_spmv(h, x.data_ptr(), y.data_ptr(), s)
+        torch.cuda.synchronize()
+        api.argcsr_destroy(h, s)
+    torch.cuda.synchronize()
+    print(f"ncu case {which}: ok")
+
+
 def main(argv=None):
     p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     p.add_argument("--gpus", type=int, default=1)
@@ -540,7 +571,12 @@ def main(argv=None):
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
+    p.add_argument("--ncu-case", choices=("small", "bench"),
+                   help="run a short untimed launch sequence for ncu, then exit")
     args = p.parse_args(argv)
+    if args.ncu_case:
+        run_ncu_case(args.ncu_case)
+        return
     args.warmup = max(3, args.warmup)   # at least three untimed warm-up steps
     if args.impl == "reference":
         run_reference(args)

@@ -78,6 +78,13 @@ __device__ __forceinline__ void subtile_tables(const uint8_t *d, int lim, int B,
 
 template <int G> constexpr int subtile_rows() { return G > 64 ? G : 64; }
 
+// Byte offset of k_groups' threadsMapping staging array in its shared memory
+// (after the parts listed at groups_smem, 4-byte aligned).
+__host__ __device__ constexpr size_t groups_pfx_offset(int T, int G) {
+    return ((size_t)T * 11 + 4 * (size_t)G + 2 * (size_t)(T / (G > 64 ? G : 64)) * G +
+            4 * (size_t)(T / (G > 64 ? G : 64)) + 3) & ~size_t(3);
+}
+
 constexpr int kTileThreads = 512;   // threads of the per-tile kernels
 
 // ---------------------------------------------------------------------------
@@ -263,6 +270,7 @@ k_groups(int n, int T, int V, const int *__restrict__ rp, const uint8_t *__restr
     uint8_t *cntA = fnA + (size_t)S * G;                            // S * G
     uint16_t *subEntry = reinterpret_cast<uint16_t *>(cntA + (size_t)S * G);  // S
     uint16_t *subBase = subEntry + S;                                         // S
+    int *pfx = reinterpret_cast<int *>(smem + groups_pfx_offset(T, G));       // T + G
     __shared__ int s_count;
     __shared__ long long s_warp[kTileThreads / 32];
 
@@ -344,7 +352,7 @@ k_groups(int n, int T, int V, const int *__restrict__ rp, const uint8_t *__restr
         for (int r = 0; r < size; ++r) {
             const unsigned l = (unsigned)L[r];
             prefix += (Cu == 0u || l <= Cu) ? 1 : (int)ceil_div_by(l, Cu, Cm);
-            threadsMapping[first + r] = prefix;
+            pfx[start + r] = prefix;   // copied out below with coalesced stores
         }
         // the record keeps the tile index beside the size (size <= 128)
         gscratch[gbase + i] = make_int4(first, size | (k << 8), 0, C <= 0x7fffffffLL ? (int)C : -1);
@@ -352,6 +360,14 @@ k_groups(int n, int T, int V, const int *__restrict__ rp, const uint8_t *__restr
         if (C > 0x7fffffffLL) flag(&tot->status, kSlotOverflow);
     }
     __syncthreads();
+    // threadsMapping of the rows this tile's groups cover: from the first
+    // start to the end of the last group (which may reach into the next tile)
+    if (count > 0) {
+        const int rowBegin = starts[0];
+        const int rowEnd = starts[count - 1] + d[starts[count - 1]];
+        for (int r = rowBegin + (int)threadIdx.x; r < rowEnd; r += blockDim.x)
+            threadsMapping[tbase + r] = pfx[r];
+    }
     // exclusive scan of chunk[i] * G -> slot offset of each group in the tile
     const int per = (count + kTileThreads - 1) / kTileThreads;
     const int i0 = min(count, (int)threadIdx.x * per), i1 = min(count, i0 + per);
@@ -502,10 +518,11 @@ k_fill(long long nGroups, int V, int n_cols, const long long *__restrict__ tileS
 
 // Dynamic shared memory of k_groups: delta (T), starts (2T), chunk sizes
 // (4T), row lengths (4(T+G)), sub-tile tables (2 S G), sub-tile entries and
-// bases (4 S).
+// bases (4 S), threadsMapping of the tile's rows (4(T+G)).
 inline size_t groups_smem(int T, int G) {
     const int S = T / (G > 64 ? G : 64);
-    return (size_t)T * 11 + 4 * (size_t)G + 2 * (size_t)S * G + 4 * (size_t)S;
+    (void)S;
+    return groups_pfx_offset(T, G) + 4 * ((size_t)T + G);
 }
 // Dynamic shared memory of k_tile_prepare: rowPointers (4(T+G+4)), delta
 // (T), sub-tile tables (2 S G).

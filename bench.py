@@ -532,6 +532,119 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# mixed-precision CG with FP64 iterative refinement (3D Poisson, 160^3)
+# ---------------------------------------------------------------------------
+
+CG_METRIC = "CG solves/s to 1e-10 relative residual (FP64 iterative refinement)"
+
+
+def cg_iteration_bytes(n, nnz, groups, sv, sw):
+    """Algorithmic bytes of one inner CG iteration: the SpMV (values +
+    columns + x + y + threadsMapping + groupInfo) and the three vector
+    kernels (p.q; x, r update with r.r; p = r + beta p) in the working type
+    of sw bytes."""
+    spmv = nnz * (sv + 4) + 2 * n * sw + 4 * n + 16 * groups
+    return spmv + 2 * n * sw + 6 * n * sw + 3 * n * sw
+
+
+def csr_cg_iteration_bytes(n, nnz):
+    return nnz * 12 + 4 * (n + 1) + 2 * n * 8 + 11 * n * 8
+
+
+def run_cg(args):
+    import torch
+    from paper_1203_5737_gb300 import argcsr as api
+    from paper_1203_5737_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream()
+    s = stream.cuda_stream
+    A = synth.laplacian_3d(160)
+    x_true = torch.from_numpy(synth.uniform_vector(A.n_cols, 5)).to(dev)
+    rp = torch.from_numpy(A.rowPointers).to(dev)
+    cols = torch.from_numpy(A.columns).to(dev)
+    v64 = torch.from_numpy(A.values).to(dev)
+    peak, peak_kind = measured_hbm_peak()
+    tol, D = 1e-10, 8
+    out = {"metric": CG_METRIC, "unit": "solves/s", "higher_is_better": True, "n_gpus": 1,
+           "dtype": "f32/bf16 inner, f64 refinement", "data": "synthetic",
+           "config": {"workload": "3D 7-point Poisson 160^3 (n 4,096,000, SPD), b = A x_true, "
+                                  "x_true ~ U[-1,1] seed 5; ARG-CSR G 32 D 8",
+                      "n": A.n_rows, "nnz": A.nnz, "tol": tol}}
+    with torch.cuda.stream(stream):
+        h64 = api.argcsr_create_from_csr(A.n_rows, A.n_cols, A.nnz, rp.data_ptr(), cols.data_ptr(),
+                                         v64.data_ptr(), api.ARGCSR_F64, GROUP_SIZE, D, 1, s)
+        b = torch.empty_like(x_true)
+        api.argcsr_spmv(h64, x_true.data_ptr(), b.data_ptr(), s)
+        variants = {}
+        for name, vals, code in (("argcsr_f32_ir", v64.float(), api.ARGCSR_F32),
+                                 ("argcsr_bf16_ir", v64.bfloat16(), api.ARGCSR_BF16),
+                                 ("argcsr_f64", v64, api.ARGCSR_F64)):
+            h = api.argcsr_create_from_csr(A.n_rows, A.n_cols, A.nnz, rp.data_ptr(), cols.data_ptr(),
+                                           vals.data_ptr(), code, GROUP_SIZE, D, 1, s)
+            variants[name] = (h, code, vals)
+        results = {}
+
+        def timed(fn, reps):
+            times, res = [], None
+            for _ in range(reps):
+                x = torch.zeros_like(x_true)
+                stream.synchronize()
+                a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                res = fn(x)
+                e.record(stream)
+                stream.synchronize()
+                times.append(a.elapsed_time(e))
+            err = float(torch.linalg.norm(x - x_true) / torch.linalg.norm(x_true))
+            return statistics.median(times), res, err
+
+        reps = max(3, args.steps // 5)
+        for name, (h, code, vals) in variants.items():
+            fn = lambda x, h=h: api.argcsr_cg_solve(h, h64, b.data_ptr(), x.data_ptr(), tol=tol,  # noqa: E731
+                                                    stream=s)
+            fn(torch.zeros_like(x_true))          # warm-up (pool, module load)
+            ms, res, err = timed(fn, reps)
+            api.argcsr_trace_begin()
+            fn(torch.zeros_like(x_true))
+            stream.synchronize()
+            api.argcsr_trace_end()
+            kern = {k: {"launches": v[0], "us_per_launch": round(v[1] * 1e3 / v[0], 2)}
+                    for k, v in api.trace_summary().items()}
+            info = api.argcsr_info(h)
+            sv = {api.ARGCSR_F64: 8, api.ARGCSR_F32: 4, api.ARGCSR_BF16: 2}[code]
+            sw = 8 if code == api.ARGCSR_F64 else 4
+            it_bytes = cg_iteration_bytes(A.n_rows, A.nnz, info.n_groups, sv, sw)
+            it_us = ms * 1e3 / max(1, res["inner_iters"])
+            results[name] = {"ms_per_solve": round(ms, 3), "solves_per_s": round(1e3 / ms, 3),
+                             **res, "x_rel_error": err,
+                             "us_per_inner_iter": round(it_us, 2),
+                             "inner_iter_gbs": round(it_bytes / (it_us * 1e-6) / 1e9, 1),
+                             "inner_iter_frac": round(it_bytes / (it_us * 1e-6) / 1e9 / peak, 4),
+                             "kernels": kern}
+        fnb = lambda x: api.argcsr_baseline_csr_cg(A.n_rows, A.nnz, rp.data_ptr(), cols.data_ptr(),  # noqa: E731
+                                                   v64.data_ptr(), b.data_ptr(), x.data_ptr(),
+                                                   tol=tol, stream=s)
+        fnb(torch.zeros_like(x_true))
+        ms, res, err = timed(fnb, reps)
+        it_bytes = csr_cg_iteration_bytes(A.n_rows, A.nnz)
+        it_us = ms * 1e3 / max(1, res["inner_iters"])
+        results["plain_csr_f64"] = {"ms_per_solve": round(ms, 3), "solves_per_s": round(1e3 / ms, 3),
+                                    **res, "x_rel_error": err, "us_per_inner_iter": round(it_us, 2),
+                                    "inner_iter_gbs": round(it_bytes / (it_us * 1e-6) / 1e9, 1),
+                                    "inner_iter_frac": round(it_bytes / (it_us * 1e-6) / 1e9 / peak, 4)}
+        for h, _, _ in variants.values():
+            api.argcsr_destroy(h, s)
+        api.argcsr_destroy(h64, s)
+    best = results["argcsr_f32_ir"]
+    out.update({"value": best["solves_per_s"], "ms_per_solve": best["ms_per_solve"],
+                "vs_plain_csr_f64": round(results["plain_csr_f64"]["ms_per_solve"] / best["ms_per_solve"], 3),
+                "peak_gbs": peak, "peak_source": peak_kind, "solvers": results})
+    print(json.dumps(out), flush=True)
+
+
 def run_ncu_case(which):
     """A short, untimed launch sequence for ncu captures: for each matrix, one
     conversion (k_tile_prepare, k_resolve, k_groups, k_tile_scan, k_fill) and
@@ -573,9 +686,15 @@ def main(argv=None):
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--ncu-case", choices=("small", "bench"),
                    help="run a short untimed launch sequence for ncu, then exit")
+    p.add_argument("--workload", choices=("uneven_fp64", "cg_poisson160"), default="uneven_fp64",
+                   help="uneven_fp64: the conversion + SpMV step (default); cg_poisson160: "
+                        "mixed-precision CG with FP64 refinement")
     args = p.parse_args(argv)
     if args.ncu_case:
         run_ncu_case(args.ncu_case)
+        return
+    if args.workload == "cg_poisson160":
+        run_cg(args)
         return
     args.warmup = max(3, args.warmup)   # at least three untimed warm-up steps
     if args.impl == "reference":

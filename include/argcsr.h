@@ -164,6 +164,61 @@ ARGCSR_API argcsr_status argcsr_device_arrays(argcsr_t A, const int32_t **d_grou
 ARGCSR_API argcsr_status argcsr_destroy(argcsr_t A, argcsr_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Iterative solution of A x = b (SPD A) with conjugate gradients on ARG-CSR.
+ * The paper names iterative solvers as the consumer of SpMV (Section 1);
+ * the solver is textbook CG with iterative refinement, not part of the
+ * paper's method.
+ *
+ * argcsr_residual: r = b - A x, with FP64 vectors and FP64 accumulation for
+ * every storage type (f32 / bf16 values are widened exactly).  d_b, d_x,
+ * d_r: f64 device arrays of n_rows / n_cols / n_rows elements.
+ *
+ * argcsr_cg_solve: iterative refinement in FP64 around an inner CG in the
+ * storage's working precision.
+ *   repeat:  r = b - A_residual x            (FP64)
+ *            stop if ||r||_2 <= tol ||b||_2
+ *            CG on A d = r / ||r||, until its residual falls by inner_tol
+ *            x += ||r|| d                     (FP64)
+ * The inner CG works in FP32 for ARGCSR_F32 / ARGCSR_BF16 storage (FP32
+ * accumulation) and in FP64 for ARGCSR_F64.  A_residual (NULL: A) supplies
+ * the FP64 residual; pass an FP64 copy when low-precision storage rounds the
+ * matrix.  d_x holds the initial guess on entry and the solution on return.
+ * All scalars stay on the device; the host reads them every check_every
+ * inner iterations.  Work arrays (4 vectors of the working type, 1 FP64
+ * vector) come from the library's pool.  Synchronous on `stream`.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    double tol;           /* target ||b - A x|| / ||b|| (> 0)                    */
+    double inner_tol;     /* inner residual reduction; 0: 1e-5 (FP32), tol (FP64) */
+    int32_t max_iters;    /* cap on inner CG iterations over the whole solve     */
+    int32_t max_outer;    /* cap on refinement steps                              */
+    int32_t check_every;  /* inner iterations between host checks; 0: 16          */
+    int32_t reserved;
+} argcsr_cg_params;
+
+typedef struct {
+    int32_t outer_iters;  /* refinement steps taken                               */
+    int32_t inner_iters;  /* CG iterations over all steps                         */
+    int32_t converged;    /* 1 if ||b - A x|| <= tol ||b|| at exit                */
+    int32_t reserved;
+    double rel_residual;  /* ||b - A x|| / ||b|| at exit (FP64, A = A_residual)   */
+} argcsr_cg_result;
+
+ARGCSR_API argcsr_status argcsr_residual(argcsr_t A, const double *d_b, const double *d_x,
+                                         double *d_r, argcsr_stream_t stream);
+ARGCSR_API argcsr_status argcsr_cg_solve(argcsr_t A, argcsr_t A_residual, const double *d_b,
+                                         double *d_x, const argcsr_cg_params *params,
+                                         argcsr_stream_t stream, argcsr_cg_result *result);
+
+/* Baseline for the solver: the same CG in FP64 with the plain CSR vector
+ * kernel (Section 2 format) as the operator; n x n matrix, f64 values. */
+ARGCSR_API argcsr_status argcsr_baseline_csr_cg(int32_t n, int64_t nnz, const int32_t *d_rowPointers,
+                                                const int32_t *d_columns, const double *d_values,
+                                                const double *d_b, double *d_x,
+                                                const argcsr_cg_params *params,
+                                                argcsr_stream_t stream, argcsr_cg_result *result);
+
+/* ---------------------------------------------------------------------------
  * argcsr_convert_noalloc -- the CSR -> ARG-CSR conversion of
  * argcsr_create_from_csr for callers that cannot allocate device memory.
  * The paper has no counterpart; this is a library facility.

@@ -37,6 +37,21 @@ class argcsr_info_t(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class argcsr_cg_params(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
+                ("max_iters", ctypes.c_int32), ("max_outer", ctypes.c_int32),
+                ("check_every", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class argcsr_cg_result(ctypes.Structure):
+    _fields_ = [("outer_iters", ctypes.c_int32), ("inner_iters", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("rel_residual", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
 class ArgcsrError(RuntimeError):
     def __init__(self, status, where):
         msg = f"{where}: {argcsr_status_string(status)}"
@@ -70,6 +85,12 @@ _SIGNATURES = {
     "argcsr_convert_noalloc": (ctypes.c_int, [_I32, _I32, _I64, _P, _P, _P, ctypes.c_int,
                                               ctypes.POINTER(argcsr_params), _P, _I64, _P, _P, _P,
                                               _I64, ctypes.POINTER(_I64), ctypes.POINTER(_I64), _P]),
+    "argcsr_residual": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "argcsr_cg_solve": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(argcsr_cg_params), _P,
+                                       ctypes.POINTER(argcsr_cg_result)]),
+    "argcsr_baseline_csr_cg": (ctypes.c_int, [_I32, _I64, _P, _P, _P, _P, _P,
+                                              ctypes.POINTER(argcsr_cg_params), _P,
+                                              ctypes.POINTER(argcsr_cg_result)]),
     "argcsr_trace_begin": (ctypes.c_int, []),
     "argcsr_trace_end": (ctypes.c_int, []),
     "argcsr_trace_kernel_count": (ctypes.c_int32, []),
@@ -205,6 +226,33 @@ def argcsr_convert_noalloc(n_rows, n_cols, nnz, d_rowPointers, d_columns, d_valu
     return st, ng.value, ns.value
 
 
+def argcsr_residual(A, d_b, d_x, d_r, stream=0) -> None:
+    _check(load_library().argcsr_residual(A, d_b, d_x, d_r, stream), "argcsr_residual")
+
+
+def _cg_params(tol, inner_tol, max_iters, max_outer, check_every):
+    return argcsr_cg_params(tol, inner_tol, max_iters, max_outer, check_every, 0)
+
+
+def argcsr_cg_solve(A, A_residual, d_b, d_x, tol=1e-10, inner_tol=0.0, max_iters=20000,
+                    max_outer=50, check_every=16, stream=0) -> dict:
+    p = _cg_params(tol, inner_tol, max_iters, max_outer, check_every)
+    r = argcsr_cg_result()
+    _check(load_library().argcsr_cg_solve(A, A_residual, d_b, d_x, ctypes.byref(p), stream,
+                                          ctypes.byref(r)), "argcsr_cg_solve")
+    return r.as_dict()
+
+
+def argcsr_baseline_csr_cg(n, nnz, d_rowPointers, d_columns, d_values, d_b, d_x, tol=1e-10,
+                           max_iters=20000, check_every=16, stream=0) -> dict:
+    p = _cg_params(tol, 0.0, max_iters, 1, check_every)
+    r = argcsr_cg_result()
+    _check(load_library().argcsr_baseline_csr_cg(n, nnz, d_rowPointers, d_columns, d_values, d_b,
+                                                 d_x, ctypes.byref(p), stream, ctypes.byref(r)),
+           "argcsr_baseline_csr_cg")
+    return r.as_dict()
+
+
 def argcsr_baseline_csr_spmv(n_rows, n_cols, nnz, d_rowPointers, d_columns, d_values, dtype,
                              variant, d_x, d_y, stream=0) -> None:
     _check(load_library().argcsr_baseline_csr_spmv(n_rows, n_cols, nnz, d_rowPointers, d_columns,
@@ -317,6 +365,31 @@ class ArgCsrMatrix:
         p = lambda a: a.ctypes.data if a.size else None  # noqa: E731
         argcsr_export(self.handle, p(gi), p(tm), p(cols), p(vals))
         return {"groupInfo": gi, "threadsMapping": tm, "columns": cols, "values": vals}
+
+    def residual(self, b, x, out=None, stream=None):
+        """r = b - A x in FP64 (b, x float64 CUDA tensors)."""
+        torch = _torch()
+        _check_cuda("b", b, torch.float64)
+        _check_cuda("x", x, torch.float64)
+        if out is None:
+            out = torch.empty(self.n_rows, dtype=torch.float64, device=b.device)
+        argcsr_residual(self.handle, _ptr(b), _ptr(x), _ptr(out), _stream(stream))
+        return out
+
+    def cg_solve(self, b, x=None, residual_matrix=None, tol=1e-10, inner_tol=0.0,
+                 max_iters=20000, max_outer=50, check_every=16, stream=None):
+        """Solve A x = b (SPD A) by CG with FP64 iterative refinement.  b and
+        x are float64 CUDA tensors; x (the initial guess, zero if None) is
+        overwritten with the solution.  Returns (x, result dict)."""
+        torch = _torch()
+        _check_cuda("b", b, torch.float64)
+        if x is None:
+            x = torch.zeros(self.n_cols, dtype=torch.float64, device=b.device)
+        _check_cuda("x", x, torch.float64)
+        R = residual_matrix.handle if residual_matrix is not None else None
+        res = argcsr_cg_solve(self.handle, R, _ptr(b), _ptr(x), tol, inner_tol, max_iters,
+                              max_outer, check_every, _stream(stream))
+        return x, res
 
     def close(self, stream=None):
         if self._h is not None:

@@ -25,10 +25,12 @@ k_csr_scalar(int n, const int *__restrict__ rp, const int *__restrict__ cols, co
     y[r] = sum;
 }
 
+// y = A x, or y = b - A x when b is given (a solver's residual)
 template <typename VT, int L>
 __global__ void __launch_bounds__(256)
 k_csr_vector(int n, const int *__restrict__ rp, const int *__restrict__ cols, const VT *__restrict__ vals,
-             const typename AccOf<VT>::type *__restrict__ x, typename AccOf<VT>::type *__restrict__ y) {
+             const typename AccOf<VT>::type *__restrict__ x, typename AccOf<VT>::type *__restrict__ y,
+             const typename AccOf<VT>::type *__restrict__ b = nullptr) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long r = t / L;
     const int l = (int)(t % L);
@@ -39,16 +41,17 @@ k_csr_vector(int n, const int *__restrict__ rp, const int *__restrict__ cols, co
     }
 #pragma unroll
     for (int o = L / 2; o; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o, L);
-    if (r < n && l == 0) y[r] = sum;
+    if (r < n && l == 0) y[r] = b ? b[r] - sum : sum;
 }
 
 template <typename VT>
 argcsr_status launch(int n, int64_t nnz, const int *rp, const int *cols, const void *vals, int variant,
-                     const void *x, void *y, cudaStream_t s) {
+                     const void *x, void *y, cudaStream_t s, const void *b = nullptr) {
     using Acc = typename AccOf<VT>::type;
     const VT *v = static_cast<const VT *>(vals);
     const Acc *xx = static_cast<const Acc *>(x);
     Acc *yy = static_cast<Acc *>(y);
+    const Acc *bb = static_cast<const Acc *>(b);
     TraceScope t(variant == 0 ? "k_csr_scalar" : "k_csr_vector", s);
     if (variant == 0) {
         k_csr_scalar<VT><<<(n + 255) / 256, 256, 0, s>>>(n, rp, cols, v, xx, yy);
@@ -59,11 +62,11 @@ argcsr_status launch(int n, int64_t nnz, const int *rp, const int *cols, const v
         const long long threads = (long long)n * L;
         const unsigned blocks = (unsigned)((threads + 255) / 256);
         switch (L) {
-            case 2: k_csr_vector<VT, 2><<<blocks, 256, 0, s>>>(n, rp, cols, v, xx, yy); break;
-            case 4: k_csr_vector<VT, 4><<<blocks, 256, 0, s>>>(n, rp, cols, v, xx, yy); break;
-            case 8: k_csr_vector<VT, 8><<<blocks, 256, 0, s>>>(n, rp, cols, v, xx, yy); break;
-            case 16: k_csr_vector<VT, 16><<<blocks, 256, 0, s>>>(n, rp, cols, v, xx, yy); break;
-            default: k_csr_vector<VT, 32><<<blocks, 256, 0, s>>>(n, rp, cols, v, xx, yy); break;
+            case 2: k_csr_vector<VT, 2><<<blocks, 256, 0, s>>>(n, rp, cols, v, xx, yy, bb); break;
+            case 4: k_csr_vector<VT, 4><<<blocks, 256, 0, s>>>(n, rp, cols, v, xx, yy, bb); break;
+            case 8: k_csr_vector<VT, 8><<<blocks, 256, 0, s>>>(n, rp, cols, v, xx, yy, bb); break;
+            case 16: k_csr_vector<VT, 16><<<blocks, 256, 0, s>>>(n, rp, cols, v, xx, yy, bb); break;
+            default: k_csr_vector<VT, 32><<<blocks, 256, 0, s>>>(n, rp, cols, v, xx, yy, bb); break;
         }
     }
     count_launches(1);
@@ -72,6 +75,21 @@ argcsr_status launch(int n, int64_t nnz, const int *rp, const int *cols, const v
 }
 
 }  // namespace
+
+argcsr_status launch_csr_vector_f64(int32_t n, int32_t n_cols, int64_t nnz, const int32_t *rp,
+                                    const int32_t *cols, const double *vals, const double *x,
+                                    double *y, cudaStream_t s) {
+    (void)n_cols;
+    return launch<double>(n, nnz, rp, cols, vals, 1, x, y, s);
+}
+
+argcsr_status launch_csr_residual_f64(int32_t n, int32_t n_cols, int64_t nnz, const int32_t *rp,
+                                      const int32_t *cols, const double *vals, const double *b,
+                                      const double *x, double *r, cudaStream_t s) {
+    (void)n_cols;
+    return launch<double>(n, nnz, rp, cols, vals, 1, x, r, s, b);
+}
+
 }  // namespace argcsr
 
 extern "C" ARGCSR_API argcsr_status argcsr_baseline_csr_spmv(

@@ -78,6 +78,17 @@ inline size_t vec_size(argcsr_dtype t) {  // element size of x and y
 
 // Defined in spmv.cu: launch the ARG-CSR SpMV kernel for a handle.
 argcsr_status launch_spmv(const argcsr_matrix *A, const void *x, void *y, cudaStream_t s);
+// Plain CSR FP64 (vector kernel): y = A x and r = b - A x.
+argcsr_status launch_csr_vector_f64(int32_t n, int32_t n_cols, int64_t nnz, const int32_t *rp,
+                                    const int32_t *cols, const double *vals, const double *x,
+                                    double *y, cudaStream_t s);
+argcsr_status launch_csr_residual_f64(int32_t n, int32_t n_cols, int64_t nnz, const int32_t *rp,
+                                      const int32_t *cols, const double *vals, const double *b,
+                                      const double *x, double *r, cudaStream_t s);
+// r = b - A x with FP64 vectors and FP64 accumulation, for any storage type
+// (stored values are widened exactly).
+argcsr_status launch_residual_f64(const argcsr_matrix *A, const double *b, const double *x,
+                                  double *r, cudaStream_t s);
 
 }  // namespace argcsr
 

@@ -108,15 +108,16 @@ __device__ __forceinline__ void add_if(float &sum, float v, bool on) {
     if (on) sum += v;
 }
 
-template <typename VT, int V, int U>
-__device__ __forceinline__ void consume(const Batch<VT, V, U> &B,
-                                        const typename AccOf<VT>::type *__restrict__ x,
-                                        typename AccOf<VT>::type &sum) {
+// sum += v * x[col] over a batch, in the accumulation type AT (values are
+// widened exactly: bf16 -> f32 -> AT, f32 -> AT).
+template <typename VT, typename AT, int V, int U>
+__device__ __forceinline__ void consume(const Batch<VT, V, U> &B, const AT *__restrict__ x,
+                                        AT &sum) {
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
         for (int e = 0; e < V; ++e)
-            if (B.c[u][e] >= 0) sum = fma(widen(B.v[u][e]), __ldg(x + B.c[u][e]), sum);
+            if (B.c[u][e] >= 0) sum = fma((AT)widen(B.v[u][e]), __ldg(x + B.c[u][e]), sum);
 }
 
 // Sum of one chunk: C/V blocks of V elements; block b of chunk c starts at
@@ -124,14 +125,12 @@ __device__ __forceinline__ void consume(const Batch<VT, V, U> &B,
 // rest are loaded only by lanes that own a row.  A minimal chunk size leaves
 // at least one chunk of the group full, so the loop runs all C/V blocks (the
 // paper's whole-warp early exit at padding would never fire).
-template <int G, typename VT, int V>
-__device__ __forceinline__ typename AccOf<VT>::type
-chunk_sum(const int *__restrict__ cols, const VT *__restrict__ vals,
-          const typename AccOf<VT>::type *__restrict__ x, long long base, int C, bool owns,
-          Batch<VT, V, (ARGCSR_SPMV_ELEMS + V - 1) / V> &B) {
-    using Acc = typename AccOf<VT>::type;
+template <int G, typename VT, typename AT, int V>
+__device__ __forceinline__ AT
+chunk_sum(const int *__restrict__ cols, const VT *__restrict__ vals, const AT *__restrict__ x,
+          long long base, int C, bool owns, Batch<VT, V, (ARGCSR_SPMV_ELEMS + V - 1) / V> &B) {
     constexpr int U = (ARGCSR_SPMV_ELEMS + V - 1) / V;
-    Acc sum = 0;
+    AT sum = 0;
     const int nb = C / V;
     const int *cp = cols + base;
     const VT *vp = vals + base;
@@ -140,10 +139,10 @@ chunk_sum(const int *__restrict__ cols, const VT *__restrict__ vals,
 #if ARGCSR_SPMV_PREFETCH
         Batch<VT, V, U> N;
         load_batch<VT, V, U>(N, cp, vp, stride, b + U, nb, owns);
-        consume<VT, V, U>(B, x, sum);
+        consume<VT, AT, V, U>(B, x, sum);
         B = N;
 #else
-        consume<VT, V, U>(B, x, sum);
+        consume<VT, AT, V, U>(B, x, sum);
         load_batch<VT, V, U>(B, cp, vp, stride, b + U, nb, owns);
 #endif
     }
@@ -151,12 +150,13 @@ chunk_sum(const int *__restrict__ cols, const VT *__restrict__ vals,
 }
 
 // G = 32: one warp per group.
-template <typename VT, int V>
+// y = A x, or y = b - A x when b is given (the residual of a solver).
+template <typename VT, typename AT, int V>
 __global__ void __launch_bounds__(256)
 k_spmv_g32(long long nGroups, const int4 *__restrict__ gi, const int *__restrict__ tm,
-           const int *__restrict__ cols, const VT *__restrict__ vals,
-           const typename AccOf<VT>::type *__restrict__ x, typename AccOf<VT>::type *__restrict__ y) {
-    using Acc = typename AccOf<VT>::type;
+           const int *__restrict__ cols, const VT *__restrict__ vals, const AT *__restrict__ x,
+           const AT *__restrict__ b, AT *__restrict__ y) {
+    using Acc = AT;
     constexpr int U = (ARGCSR_SPMV_ELEMS + V - 1) / V;
     const int lane = threadIdx.x & 31;
     const long long g = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -173,7 +173,7 @@ k_spmv_g32(long long nGroups, const int4 *__restrict__ gi, const int *__restrict
     const unsigned below = ends & ((1u << lane) - 1u);
     const int row = __popc(below);          // local row of this lane's chunk
     const bool owns = row < size;           // false for free chunks
-    Acc sum = chunk_sum<32, VT, V>(cols, vals, x, base, C, owns, B);
+    Acc sum = chunk_sum<32, VT, AT, V>(cols, vals, x, base, C, owns, B);
     // Segmented tree reduction of the partial sums into the first lane of
     // each row: a row of t chunks costs t - 1 FP64 adds (FP64 throughput on
     // GB300 is about 2 operations per clock per SM, the same budget the FMAs
@@ -187,16 +187,16 @@ k_spmv_g32(long long nGroups, const int4 *__restrict__ gi, const int *__restrict
         const Acc v = __shfl_down_sync(FULL, sum, o);
         add_if(sum, v, ((lane - segStart) & (2 * o - 1)) == 0 && lane + o < segEnd);
     }
-    if (owns && lane == segStart) y[first + row] = sum;
+    if (owns && lane == segStart) y[first + row] = b ? b[first + row] - sum : sum;
 }
 
 // G = 64 or 128: one group per G threads, 256 / G groups per block.
-template <int G, typename VT, int V>
+template <int G, typename VT, typename AT, int V>
 __global__ void __launch_bounds__(256)
 k_spmv_block(long long nGroups, const int4 *__restrict__ gi, const int *__restrict__ tm,
-             const int *__restrict__ cols, const VT *__restrict__ vals,
-             const typename AccOf<VT>::type *__restrict__ x, typename AccOf<VT>::type *__restrict__ y) {
-    using Acc = typename AccOf<VT>::type;
+             const int *__restrict__ cols, const VT *__restrict__ vals, const AT *__restrict__ x,
+             const AT *__restrict__ b, AT *__restrict__ y) {
+    using Acc = AT;
     constexpr int GPB = 256 / G;
     __shared__ Acc partial[256];
     __shared__ int rowOf[256];
@@ -219,56 +219,65 @@ k_spmv_block(long long nGroups, const int4 *__restrict__ gi, const int *__restri
     const long long base = (long long)info.z + c * V;
     Batch<VT, V, U> B;
     load_batch<VT, V, U>(B, cols + base, vals + base, (long long)G * V, 0, C / V, owns);
-    partial[threadIdx.x] = chunk_sum<G, VT, V>(cols, vals, x, base, C, owns, B);
+    partial[threadIdx.x] = chunk_sum<G, VT, AT, V>(cols, vals, x, base, C, owns, B);
     __syncthreads();
     if (c < size) {
         Acc s = partial[sub * G + begin];
         for (int k = begin + 1; k < end; ++k) s += partial[sub * G + k];
-        y[first + c] = s;
+        y[first + c] = b ? b[first + c] - s : s;
     }
 }
 
-template <typename VT, int V>
-argcsr_status launch_typed(const argcsr_matrix *A, const void *x, void *y, cudaStream_t s) {
-    using Acc = typename AccOf<VT>::type;
+template <typename VT, typename AT, int V>
+argcsr_status launch_typed(const argcsr_matrix *A, const void *x, const void *b, void *y,
+                           cudaStream_t s) {
     const long long ng = A->n_groups;
     const auto *gi = A->d_groupInfo;
     const auto *tm = A->d_threadsMapping;
     const auto *cols = A->d_columns;
     const auto *vals = static_cast<const VT *>(A->d_values);
-    const auto *xx = static_cast<const Acc *>(x);
-    auto *yy = static_cast<Acc *>(y);
-    TraceScope t(A->G == 32 ? "k_spmv_g32" : "k_spmv_block", s);
+    const auto *xx = static_cast<const AT *>(x);
+    const auto *bb = static_cast<const AT *>(b);
+    auto *yy = static_cast<AT *>(y);
+    TraceScope t(A->G == 32 ? (b ? "k_residual_g32" : "k_spmv_g32")
+                            : (b ? "k_residual_block" : "k_spmv_block"), s);
     switch (A->G) {
-        case 32: k_spmv_g32<VT, V><<<(unsigned)((ng + 7) / 8), 256, 0, s>>>(ng, gi, tm, cols, vals, xx, yy); break;
-        case 64: k_spmv_block<64, VT, V><<<(unsigned)((ng + 3) / 4), 256, 0, s>>>(ng, gi, tm, cols, vals, xx, yy); break;
-        default: k_spmv_block<128, VT, V><<<(unsigned)((ng + 1) / 2), 256, 0, s>>>(ng, gi, tm, cols, vals, xx, yy); break;
+        case 32: k_spmv_g32<VT, AT, V><<<(unsigned)((ng + 7) / 8), 256, 0, s>>>(ng, gi, tm, cols, vals, xx, bb, yy); break;
+        case 64: k_spmv_block<64, VT, AT, V><<<(unsigned)((ng + 3) / 4), 256, 0, s>>>(ng, gi, tm, cols, vals, xx, bb, yy); break;
+        default: k_spmv_block<128, VT, AT, V><<<(unsigned)((ng + 1) / 2), 256, 0, s>>>(ng, gi, tm, cols, vals, xx, bb, yy); break;
     }
     count_launches(1);
     ARGCSR_CHECK_LAUNCH("argcsr_spmv kernel");
     return ARGCSR_OK;
 }
 
-template <typename VT>
-argcsr_status launch_v(const argcsr_matrix *A, const void *x, void *y, cudaStream_t s) {
+template <typename VT, typename AT>
+argcsr_status launch_v(const argcsr_matrix *A, const void *x, const void *b, void *y, cudaStream_t s) {
     switch (A->V) {
-        case 1: return launch_typed<VT, 1>(A, x, y, s);
-        case 2: return launch_typed<VT, 2>(A, x, y, s);
-        default: return launch_typed<VT, 4>(A, x, y, s);
+        case 1: return launch_typed<VT, AT, 1>(A, x, b, y, s);
+        case 2: return launch_typed<VT, AT, 2>(A, x, b, y, s);
+        default: return launch_typed<VT, AT, 4>(A, x, b, y, s);
     }
 }
 
 }  // namespace
 
 argcsr_status launch_spmv(const argcsr_matrix *A, const void *x, void *y, cudaStream_t s) {
-    if (A->n_groups == 0) {
-        // every group is empty only if there are no rows
-        return ARGCSR_OK;
-    }
+    if (A->n_groups == 0) return ARGCSR_OK;   // no rows
     switch (A->dtype) {
-        case ARGCSR_F64: return launch_v<double>(A, x, y, s);
-        case ARGCSR_F32: return launch_v<float>(A, x, y, s);
-        default: return launch_v<uint16_t>(A, x, y, s);
+        case ARGCSR_F64: return launch_v<double, double>(A, x, nullptr, y, s);
+        case ARGCSR_F32: return launch_v<float, float>(A, x, nullptr, y, s);
+        default: return launch_v<uint16_t, float>(A, x, nullptr, y, s);
+    }
+}
+
+argcsr_status launch_residual_f64(const argcsr_matrix *A, const double *b, const double *x,
+                                  double *r, cudaStream_t s) {
+    if (A->n_groups == 0) return ARGCSR_OK;
+    switch (A->dtype) {
+        case ARGCSR_F64: return launch_v<double, double>(A, x, b, r, s);
+        case ARGCSR_F32: return launch_v<float, double>(A, x, b, r, s);
+        default: return launch_v<uint16_t, double>(A, x, b, r, s);
     }
 }
 

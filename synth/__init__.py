@@ -25,7 +25,7 @@ import numpy as np
 
 __all__ = [
     "Csr", "laplacian_2d", "laplacian_3d", "lognormal_rows", "zipf_rows",
-    "banded", "block_diag", "random_csr", "fig3_example", "uniform_vector",
+    "banded", "block_diag", "random_csr", "spd_random", "fig3_example", "uniform_vector",
     "pathological_overflow_rowpointers", "workload",
 ]
 
@@ -214,6 +214,32 @@ def random_csr(n_rows: int, n_cols: int, seed: int, mean_len: float = 4.0,
     cols = _distinct_sorted_columns(rng, lengths, n_cols)
     vals = rng.standard_normal(int(lengths.sum())).astype(dtype)
     return _from_lengths(n_rows, n_cols, lengths, cols, vals, f"random_{n_rows}x{n_cols}_s{seed}")
+
+
+def spd_random(n: int, mean_len: float = 8.0, seed: int = 0, dtype=np.float64) -> Csr:
+    """Symmetric, strictly diagonally dominant sparse matrix (hence SPD):
+    random off-diagonal pairs a_ij = a_ji ~ N(0, 1) (about mean_len per row),
+    diagonal 1 + sum_j |a_ij|."""
+    rng = np.random.default_rng(seed)
+    m = int(n * mean_len / 2)
+    i = rng.integers(0, n, m)
+    j = rng.integers(0, n, m)
+    keep = i != j
+    lo, hi = np.minimum(i[keep], j[keep]), np.maximum(i[keep], j[keep])
+    _, first = np.unique(lo.astype(np.int64) * n + hi, return_index=True)  # one value per pair
+    lo, hi = lo[first], hi[first]
+    v = rng.standard_normal(lo.size)
+    rows = np.concatenate([lo, hi])
+    cols = np.concatenate([hi, lo])
+    vals = np.concatenate([v, v])
+    diag = 1.0 + np.bincount(rows, weights=np.abs(vals), minlength=n)
+    rows = np.concatenate([rows, np.arange(n)])
+    cols = np.concatenate([cols, np.arange(n)])
+    vals = np.concatenate([vals, diag])
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    lengths = np.bincount(rows, minlength=n)
+    return _from_lengths(n, n, lengths, cols, vals.astype(dtype), f"spd_random_{n}")
 
 
 def fig3_example(dtype=np.float64) -> Csr:

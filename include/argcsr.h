@@ -56,6 +56,8 @@ typedef enum {
 
 typedef struct CUstream_st *argcsr_stream_t;
 typedef struct argcsr_matrix *argcsr_t;
+typedef struct argcsr_batch *argcsr_batch_t;
+typedef struct argcsr_graph *argcsr_graph_t;
 
 /* Conversion parameters (Section 3).
  *   group_size          G, the number of chunks per group; the paper's
@@ -162,6 +164,65 @@ ARGCSR_API argcsr_status argcsr_device_arrays(argcsr_t A, const int32_t **d_grou
  * itself.  NULL-safe.  Work already queued on other streams that reads the
  * handle must be ordered before `stream` by the caller. */
 ARGCSR_API argcsr_status argcsr_destroy(argcsr_t A, argcsr_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * argcsr_spmm -- Y = A X for k right-hand sides (k in {1, 2, 4, 8, 16}).
+ * The Section 4 kernel with k multiply-adds per slot: X is n_cols x k and Y
+ * is n_rows x k, row-major with leading dimensions ldx, ldy >= k (elements);
+ * element type as for argcsr_spmv.  X and Y must not overlap.  16-byte
+ * aligned arrays with ld * element size a multiple of 16 use vector loads.
+ * Asynchronous on `stream`; one kernel.
+ * ------------------------------------------------------------------------ */
+ARGCSR_API argcsr_status argcsr_spmm(argcsr_t A, int32_t k, const void *d_X, int64_t ldx,
+                                     void *d_Y, int64_t ldy, argcsr_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Batches: products of many independent matrices in one persistent launch.
+ *
+ * argcsr_batch_create borrows `count` handles (they must outlive the batch;
+ * all with group_size 32 -- ARGCSR_ENOTSUP otherwise -- and the same dtype
+ * and vec_width).  Right-hand sides and results are packed in matrix order:
+ * matrix i's X block starts at row col_offsets[i] of an (sum n_cols) x k
+ * row-major array, its Y block at row row_offsets[i] of (sum n_rows) x k
+ * (argcsr_batch_offsets returns both prefix sums, count + 1 entries each).
+ * argcsr_batch_spmm runs every group of every matrix in one launch with a
+ * fixed grid (8 blocks of 8 warps per SM); warps take contiguous runs of the
+ * concatenated group list.  argcsr_batch_graph_create captures that launch
+ * (for fixed X, Y and k) in a CUDA graph replayed by argcsr_graph_launch.
+ * ------------------------------------------------------------------------ */
+ARGCSR_API argcsr_status argcsr_batch_create(int32_t count, const argcsr_t *mats,
+                                             argcsr_stream_t stream, argcsr_batch_t *out);
+ARGCSR_API argcsr_status argcsr_batch_info(argcsr_batch_t batch, int64_t *total_rows,
+                                           int64_t *total_cols, int64_t *total_groups,
+                                           int64_t *total_nnz, int64_t *total_slots);
+ARGCSR_API argcsr_status argcsr_batch_offsets(argcsr_batch_t batch, int64_t *h_row_offsets,
+                                              int64_t *h_col_offsets);
+ARGCSR_API argcsr_status argcsr_batch_spmm(argcsr_batch_t batch, int32_t k, const void *d_X,
+                                           void *d_Y, argcsr_stream_t stream);
+ARGCSR_API argcsr_status argcsr_batch_graph_create(argcsr_batch_t batch, int32_t k,
+                                                   const void *d_X, void *d_Y,
+                                                   argcsr_graph_t *out);
+ARGCSR_API argcsr_status argcsr_graph_launch(argcsr_graph_t graph, argcsr_stream_t stream);
+ARGCSR_API argcsr_status argcsr_graph_destroy(argcsr_graph_t graph);
+ARGCSR_API argcsr_status argcsr_batch_destroy(argcsr_batch_t batch, argcsr_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * argcsr_autotune -- choose group_size and desired_chunk_size for a matrix
+ * by measurement.  The paper reports that the best desiredChunkSize depends
+ * on the matrix (Section 5: regular matrices want large values, irregular
+ * ones small) and uses 128 threads per block; this call converts the CSR
+ * input with every candidate (G in the bits of group_size_mask: 1 = 32,
+ * 2 = 64, 4 = 128; D in {1, 2, 3, 4, 6, 8, 12, 16, 32}; V = 1), times
+ * `reps` products with k right-hand sides, and returns the fastest in *best
+ * (its time per product in *best_us).  Candidates whose layout has the same
+ * size as one already timed are skipped.  Synchronous on `stream`.
+ * ------------------------------------------------------------------------ */
+ARGCSR_API argcsr_status argcsr_autotune(int32_t n_rows, int32_t n_cols, int64_t nnz,
+                                         const int32_t *d_rowPointers, const int32_t *d_columns,
+                                         const void *d_values, argcsr_dtype dtype, int32_t k,
+                                         int32_t group_size_mask, int32_t reps,
+                                         argcsr_stream_t stream, argcsr_params *best,
+                                         float *best_us);
 
 /* ---------------------------------------------------------------------------
  * Iterative solution of A x = b (SPD A) with conjugate gradients on ARG-CSR.

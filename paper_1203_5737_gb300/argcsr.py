@@ -91,6 +91,18 @@ _SIGNATURES = {
     "argcsr_baseline_csr_cg": (ctypes.c_int, [_I32, _I64, _P, _P, _P, _P, _P,
                                               ctypes.POINTER(argcsr_cg_params), _P,
                                               ctypes.POINTER(argcsr_cg_result)]),
+    "argcsr_spmm": (ctypes.c_int, [_P, _I32, _P, _I64, _P, _I64, _P]),
+    "argcsr_batch_create": (ctypes.c_int, [_I32, ctypes.POINTER(_P), _P, ctypes.POINTER(_P)]),
+    "argcsr_batch_info": (ctypes.c_int, [_P] + [ctypes.POINTER(_I64)] * 5),
+    "argcsr_batch_offsets": (ctypes.c_int, [_P, _P, _P]),
+    "argcsr_batch_spmm": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
+    "argcsr_batch_graph_create": (ctypes.c_int, [_P, _I32, _P, _P, ctypes.POINTER(_P)]),
+    "argcsr_graph_launch": (ctypes.c_int, [_P, _P]),
+    "argcsr_graph_destroy": (ctypes.c_int, [_P]),
+    "argcsr_batch_destroy": (ctypes.c_int, [_P, _P]),
+    "argcsr_autotune": (ctypes.c_int, [_I32, _I32, _I64, _P, _P, _P, ctypes.c_int, _I32, _I32, _I32,
+                                       _P, ctypes.POINTER(argcsr_params),
+                                       ctypes.POINTER(ctypes.c_float)]),
     "argcsr_trace_begin": (ctypes.c_int, []),
     "argcsr_trace_end": (ctypes.c_int, []),
     "argcsr_trace_kernel_count": (ctypes.c_int32, []),
@@ -224,6 +236,67 @@ def argcsr_convert_noalloc(n_rows, n_cols, nnz, d_rowPointers, d_columns, d_valu
         d_groupInfo, group_capacity, d_threadsMapping, d_out_columns, d_out_values, slot_capacity,
         ctypes.byref(ng), ctypes.byref(ns), stream)
     return st, ng.value, ns.value
+
+
+def argcsr_spmm(A, k, d_X, ldx, d_Y, ldy, stream=0) -> None:
+    _check(load_library().argcsr_spmm(A, k, d_X, ldx, d_Y, ldy, stream), "argcsr_spmm")
+
+
+def argcsr_batch_create(handles, stream=0) -> int:
+    arr = (ctypes.c_void_p * len(handles))(*handles)
+    out = ctypes.c_void_p()
+    _check(load_library().argcsr_batch_create(len(handles), arr, stream, ctypes.byref(out)),
+           "argcsr_batch_create")
+    return out.value
+
+
+def argcsr_batch_info(B) -> dict:
+    vals = [ctypes.c_int64() for _ in range(5)]
+    _check(load_library().argcsr_batch_info(B, *[ctypes.byref(v) for v in vals]), "argcsr_batch_info")
+    keys = ("total_rows", "total_cols", "total_groups", "total_nnz", "total_slots")
+    return {k: v.value for k, v in zip(keys, vals)}
+
+
+def argcsr_batch_offsets(B, count):
+    rows = np.empty(count + 1, dtype=np.int64)
+    cols = np.empty(count + 1, dtype=np.int64)
+    _check(load_library().argcsr_batch_offsets(B, rows.ctypes.data, cols.ctypes.data),
+           "argcsr_batch_offsets")
+    return rows, cols
+
+
+def argcsr_batch_spmm(B, k, d_X, d_Y, stream=0) -> None:
+    _check(load_library().argcsr_batch_spmm(B, k, d_X, d_Y, stream), "argcsr_batch_spmm")
+
+
+def argcsr_batch_graph_create(B, k, d_X, d_Y) -> int:
+    out = ctypes.c_void_p()
+    _check(load_library().argcsr_batch_graph_create(B, k, d_X, d_Y, ctypes.byref(out)),
+           "argcsr_batch_graph_create")
+    return out.value
+
+
+def argcsr_graph_launch(G, stream=0) -> None:
+    _check(load_library().argcsr_graph_launch(G, stream), "argcsr_graph_launch")
+
+
+def argcsr_graph_destroy(G) -> None:
+    _check(load_library().argcsr_graph_destroy(G), "argcsr_graph_destroy")
+
+
+def argcsr_batch_destroy(B, stream=0) -> None:
+    _check(load_library().argcsr_batch_destroy(B, stream), "argcsr_batch_destroy")
+
+
+def argcsr_autotune(n_rows, n_cols, nnz, d_rowPointers, d_columns, d_values, dtype, k=1,
+                    group_size_mask=7, reps=10, stream=0):
+    """Returns ((group_size, desired_chunk_size, vec_width), microseconds)."""
+    best = argcsr_params()
+    us = ctypes.c_float()
+    _check(load_library().argcsr_autotune(n_rows, n_cols, nnz, d_rowPointers, d_columns, d_values,
+                                          dtype, k, group_size_mask, reps, stream,
+                                          ctypes.byref(best), ctypes.byref(us)), "argcsr_autotune")
+    return (best.group_size, best.desired_chunk_size, best.vec_width), us.value
 
 
 def argcsr_residual(A, d_b, d_x, d_r, stream=0) -> None:
@@ -365,6 +438,21 @@ class ArgCsrMatrix:
         p = lambda a: a.ctypes.data if a.size else None  # noqa: E731
         argcsr_export(self.handle, p(gi), p(tm), p(cols), p(vals))
         return {"groupInfo": gi, "threadsMapping": tm, "columns": cols, "values": vals}
+
+    def spmm(self, X, out=None, stream=None):
+        """Y = A X for X of shape (n_cols, k), k in {1, 2, 4, 8, 16}; any
+        row stride (X.stride(0) >= k, unit column stride)."""
+        torch = _torch()
+        if X.dim() != 2 or X.shape[0] != self.n_cols or X.stride(1) != 1 or X.dtype != self.vector_dtype:
+            raise ValueError("X must be (n_cols, k) with unit column stride and the vector dtype")
+        if not X.is_cuda:
+            raise ValueError("X must be a CUDA tensor")
+        k = X.shape[1]
+        if out is None:
+            out = torch.empty((self.n_rows, k), dtype=self.vector_dtype, device=X.device)
+        argcsr_spmm(self.handle, k, X.data_ptr(), X.stride(0), out.data_ptr(), out.stride(0),
+                    _stream(stream))
+        return out
 
     def residual(self, b, x, out=None, stream=None):
         """r = b - A x in FP64 (b, x float64 CUDA tensors)."""

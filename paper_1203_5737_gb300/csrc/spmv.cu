@@ -23,45 +23,11 @@
 //    (column -1) rather than by a whole-warp exit: with the minimal chunk
 //    size some chunk of every group is full, so a warp never runs out of
 //    work before the last element row.
+#include "device.cuh"
 #include "internal.cuh"
 
 namespace argcsr {
 namespace {
-
-constexpr unsigned FULL = 0xffffffffu;
-
-template <typename VT> struct AccOf { using type = float; };
-template <> struct AccOf<double> { using type = double; };
-
-__device__ __forceinline__ double widen(double v) { return v; }
-__device__ __forceinline__ float widen(float v) { return v; }
-__device__ __forceinline__ float widen(uint16_t bits) { return __uint_as_float((unsigned)bits << 16); }
-
-// Streaming (evict-first) loads of V consecutive elements, V*sizeof(T) in
-// {2, 4, 8, 16, 32} bytes, from an address aligned to that size.
-template <typename T, int V>
-__device__ __forceinline__ void ld_stream(const T *p, T (&out)[V]) {
-    constexpr int B = (int)sizeof(T) * V;
-    if constexpr (B == 2) {
-        unsigned short u = __ldcs(reinterpret_cast<const unsigned short *>(p));
-        memcpy(out, &u, 2);
-    } else if constexpr (B == 4) {
-        unsigned u = __ldcs(reinterpret_cast<const unsigned *>(p));
-        memcpy(out, &u, 4);
-    } else if constexpr (B == 8) {
-        uint2 u = __ldcs(reinterpret_cast<const uint2 *>(p));
-        memcpy(out, &u, 8);
-    } else if constexpr (B == 16) {
-        uint4 u = __ldcs(reinterpret_cast<const uint4 *>(p));
-        memcpy(out, &u, 16);
-    } else {
-        static_assert(B == 32, "unsupported vector width");
-        uint4 u0 = __ldcs(reinterpret_cast<const uint4 *>(p));
-        uint4 u1 = __ldcs(reinterpret_cast<const uint4 *>(p) + 1);
-        memcpy(out, &u0, 16);
-        memcpy(reinterpret_cast<char *>(out) + 16, &u1, 16);
-    }
-}
 
 #ifndef ARGCSR_SPMV_ELEMS
 #define ARGCSR_SPMV_ELEMS 4      // elements per lane per batch
@@ -95,17 +61,6 @@ __device__ __forceinline__ void load_batch(Batch<VT, V, U> &B, const int *__rest
             for (int e = 0; e < V; ++e) { B.c[u][e] = -1; B.v[u][e] = VT(0); }
         }
     }
-}
-
-// sum += v on lanes where `on` holds.  Written as a predicated PTX add so
-// that lanes without work issue no FP64 operation (a plain conditional add
-// may be turned into an add on every lane followed by a select).
-__device__ __forceinline__ void add_if(double &sum, double v, bool on) {
-    asm("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p add.rn.f64 %0, %0, %1;\n\t}"
-        : "+d"(sum) : "d"(v), "r"((unsigned)on));
-}
-__device__ __forceinline__ void add_if(float &sum, float v, bool on) {
-    if (on) sum += v;
 }
 
 // sum += v * x[col] over a batch, in the accumulation type AT (values are

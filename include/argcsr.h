@@ -186,8 +186,11 @@ ARGCSR_API argcsr_status argcsr_spmm(argcsr_t A, int32_t k, const void *d_X, int
  * row-major array, its Y block at row row_offsets[i] of (sum n_rows) x k
  * (argcsr_batch_offsets returns both prefix sums, count + 1 entries each).
  * argcsr_batch_spmm runs every group of every matrix in one launch with a
- * fixed grid (8 blocks of 8 warps per SM); warps take contiguous runs of the
- * concatenated group list.  argcsr_batch_graph_create captures that launch
+ * fixed grid (two waves of the blocks that fit on the SMs); warps take
+ * contiguous runs of the concatenated group list for k < 4 and stride
+ * through it for k >= 4 (rows of X stay in cache while all warps sweep the
+ * same few matrices).  X and Y must be 16-byte aligned.
+ * argcsr_batch_graph_create captures that launch
  * (for fixed X, Y and k) in a CUDA graph replayed by argcsr_graph_launch.
  * ------------------------------------------------------------------------ */
 ARGCSR_API argcsr_status argcsr_batch_create(int32_t count, const argcsr_t *mats,
@@ -223,6 +226,19 @@ ARGCSR_API argcsr_status argcsr_autotune(int32_t n_rows, int32_t n_cols, int64_t
                                          int32_t group_size_mask, int32_t reps,
                                          argcsr_stream_t stream, argcsr_params *best,
                                          float *best_us);
+
+/* argcsr_autotune_batch -- the same search for a batch: for every
+ * candidate desiredChunkSize in {1, 2, 4, 8, 16, 32} (G = 32, V = 1) convert
+ * all `count` matrices, time `reps` argcsr_batch_spmm launches with k
+ * right-hand sides, keep the fastest.  Matrix i is given by host arrays of
+ * sizes and of device pointers to its CSR arrays.  Synchronous. */
+ARGCSR_API argcsr_status argcsr_autotune_batch(int32_t count, const int32_t *h_n_rows,
+                                               const int32_t *h_n_cols, const int64_t *h_nnz,
+                                               const int32_t *const *h_rowPointers,
+                                               const int32_t *const *h_columns,
+                                               const void *const *h_values, argcsr_dtype dtype,
+                                               int32_t k, int32_t reps, argcsr_stream_t stream,
+                                               argcsr_params *best, float *best_us);
 
 /* ---------------------------------------------------------------------------
  * Iterative solution of A x = b (SPD A) with conjugate gradients on ARG-CSR.

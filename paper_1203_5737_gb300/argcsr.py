@@ -103,6 +103,9 @@ _SIGNATURES = {
     "argcsr_autotune": (ctypes.c_int, [_I32, _I32, _I64, _P, _P, _P, ctypes.c_int, _I32, _I32, _I32,
                                        _P, ctypes.POINTER(argcsr_params),
                                        ctypes.POINTER(ctypes.c_float)]),
+    "argcsr_autotune_batch": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P, _P, ctypes.c_int, _I32, _I32,
+                                             _P, ctypes.POINTER(argcsr_params),
+                                             ctypes.POINTER(ctypes.c_float)]),
     "argcsr_trace_begin": (ctypes.c_int, []),
     "argcsr_trace_end": (ctypes.c_int, []),
     "argcsr_trace_kernel_count": (ctypes.c_int32, []),
@@ -296,6 +299,24 @@ def argcsr_autotune(n_rows, n_cols, nnz, d_rowPointers, d_columns, d_values, dty
     _check(load_library().argcsr_autotune(n_rows, n_cols, nnz, d_rowPointers, d_columns, d_values,
                                           dtype, k, group_size_mask, reps, stream,
                                           ctypes.byref(best), ctypes.byref(us)), "argcsr_autotune")
+    return (best.group_size, best.desired_chunk_size, best.vec_width), us.value
+
+
+def argcsr_autotune_batch(n_rows, n_cols, nnz, rp_ptrs, col_ptrs, val_ptrs, dtype, k=1, reps=5,
+                          stream=0):
+    """Batch-level search over desiredChunkSize (G 32).  The per-matrix
+    arguments are sequences of equal length.  Returns ((G, D, V), us)."""
+    c = len(n_rows)
+    a32 = lambda v: np.ascontiguousarray(v, dtype=np.int32)  # noqa: E731
+    nr, nc, nz = a32(n_rows), a32(n_cols), np.ascontiguousarray(nnz, dtype=np.int64)
+    pr, pc, pv = (np.ascontiguousarray([p or 0 for p in ps], dtype=np.uint64)
+                  for ps in (rp_ptrs, col_ptrs, val_ptrs))
+    best = argcsr_params()
+    us = ctypes.c_float()
+    _check(load_library().argcsr_autotune_batch(c, nr.ctypes.data, nc.ctypes.data, nz.ctypes.data,
+                                                pr.ctypes.data, pc.ctypes.data, pv.ctypes.data,
+                                                dtype, k, reps, stream, ctypes.byref(best),
+                                                ctypes.byref(us)), "argcsr_autotune_batch")
     return (best.group_size, best.desired_chunk_size, best.vec_width), us.value
 
 

@@ -9,9 +9,9 @@
 // come with one or a few vector loads.
 //
 // The batch kernel runs the G = 32 warp-per-group body over the groups of
-// all matrices of a batch: warps take contiguous runs of the concatenated
-// group list, so a launch has a fixed grid (a few blocks per SM) whatever the
-// number and sizes of the matrices, and can be captured once in a CUDA graph.
+// all matrices of a batch: warps share out the concatenated group list,
+// so a launch has a fixed grid (a few blocks per SM) whatever the number and
+// sizes of the matrices, and can be captured once in a CUDA graph.
 #include <math.h>
 
 #include <vector>
@@ -197,37 +197,148 @@ k_spmm_block(long long nGroups, const int4 *__restrict__ gi, const int *__restri
     }
 }
 
-// All groups of a batch of G = 32 matrices.  Warp w takes the run
-// [w*per, (w+1)*per) of the concatenated group list and walks the matrix
-// index forward as it crosses matrix boundaries.
-template <typename VT, typename AT, int K, int V, bool VEC>
+// Phases of one G = 32 group, so that a warp can interleave two groups:
+// (1) issue the threadsMapping load and the group's first slot rows,
+// (2) find the lane's row, gather x and accumulate (remaining slot rows
+//     follow), (3) reduce per row and store.
+template <typename VT, typename AT, int K, int V>
+struct GroupWork {
+    static constexpr int U = V >= 4 ? 1 : 4 / V;   // V-blocks loaded in phase 1
+    int4 info;
+    const int *tm;
+    const int *cols;
+    const VT *vals;
+    const AT *X;
+    AT *Y;
+    int tmv;
+    int c[U][V];
+    VT v[U][V];
+    AT acc[K];
+
+    __device__ __forceinline__ void issue(int lane) {
+        const int size = info.y, nb = info.w / V;
+        tmv = lane < size ? __ldg(tm + info.x + lane) : 0;
+        const long long base = (long long)info.z + lane * V;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (u < nb) {
+                ld_stream<int, V>(cols + base + (long long)u * 32 * V, c[u]);
+                ld_stream<VT, V>(vals + base + (long long)u * 32 * V, v[u]);
+            } else {
+#pragma unroll
+                for (int e = 0; e < V; ++e) c[u][e] = -1;
+            }
+        }
+    }
+    __device__ __forceinline__ void slot(int col, VT val) {
+        if (col >= 0) {
+            AT xv[K];
+            load_x_row<AT, K, (K % 4 == 0 || (sizeof(AT) == 8 && K % 2 == 0))>(X + (long long)col * K, xv);
+            const AT a = (AT)widen(val);
+#pragma unroll
+            for (int q = 0; q < K; ++q) acc[q] = fma(a, xv[q], acc[q]);
+        }
+    }
+    __device__ __forceinline__ void finish(int lane) {
+        const int size = info.y, nb = info.w / V;
+        const unsigned ends = __reduce_or_sync(FULL, lane < size ? 1u << (tmv - 1) : 0u);
+        const unsigned below = ends & ((1u << lane) - 1u);
+        const int row = __popc(below);
+        const bool owns = row < size;
+        const int segStart = below ? 32 - __clz(below) : 0;
+        const unsigned atOrAbove = ends & ~((1u << lane) - 1u);
+        const int segEnd = atOrAbove ? __ffs(atOrAbove) : 0;
+#pragma unroll
+        for (int q = 0; q < K; ++q) acc[q] = 0;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int e = 0; e < V; ++e) slot(owns ? c[u][e] : -1, v[u][e]);
+        const long long base = (long long)info.z + lane * V;
+        for (int b = U; b < nb; ++b) {
+            if (!owns) break;
+            int cc[V];
+            VT vv[V];
+            ld_stream<int, V>(cols + base + (long long)b * 32 * V, cc);
+            ld_stream<VT, V>(vals + base + (long long)b * 32 * V, vv);
+#pragma unroll
+            for (int e = 0; e < V; ++e) slot(cc[e], vv[e]);
+        }
+        const int maxChunks = __reduce_max_sync(FULL, owns ? segEnd - segStart : 0);
+        for (int o = 1; o < maxChunks; o <<= 1) {
+            const bool on = ((lane - segStart) & (2 * o - 1)) == 0 && lane + o < segEnd;
+#pragma unroll
+            for (int q = 0; q < K; ++q) {
+                const AT t = __shfl_down_sync(FULL, acc[q], o);
+                add_if(acc[q], t, on);
+            }
+        }
+        if (owns && lane == segStart)
+            store_y_row<AT, K, (sizeof(AT) == 4 && K % 4 == 0)>(Y + (long long)(info.x + row) * K, acc);
+    }
+};
+
+// All groups of a batch of G = 32 matrices in one launch.  Two ways to
+// share the concatenated group list among the W warps of the grid:
+//  * STRIPED (k >= 4): warp w takes groups w, w + W, w + 2W, ...; the warps
+//    sweep the batch together, so only the few matrices under the current
+//    window are live and their rows of X (k values each) stay in L1/L2;
+//  * contiguous (k < 4): warp w takes one run of consecutive groups; its
+//    matrix data streams in order, which wins when X rows are small.
+// Each warp works on two groups at a time (their loads are issued before
+// either is consumed): batch groups are small, so the chain of dependent
+// loads of a group, not bandwidth, bounds a warp.  Packed X and Y have
+// leading dimension K.
+template <typename VT, typename AT, int K, int V, bool STRIPED>
 __global__ void __launch_bounds__(256)
 k_batch_spmm_g32(const BatchDesc *__restrict__ desc, const long long *__restrict__ groupPrefix,
                  int nMat, long long totalGroups, const AT *__restrict__ X, AT *__restrict__ Y) {
     const int lane = threadIdx.x & 31;
     const long long W = (long long)gridDim.x * 8;
     const long long w = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
-    const long long per = (totalGroups + W - 1) / W;
-    const long long g0 = w * per, g1 = min(totalGroups, g0 + per);
-    if (g0 >= g1) return;
-    int lo = 0, hi = nMat - 1;   // the matrix holding g0: last m with prefix[m] <= g0
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (groupPrefix[mid] <= g0) lo = mid; else hi = mid - 1;
-    }
-    int m = lo;
-    BatchDesc d = desc[m];
-    long long mEnd = groupPrefix[m + 1];
-    for (long long g = g0; g < g1; ++g) {
-        while (g >= mEnd) {
-            ++m;
-            d = desc[m];
-            mEnd = groupPrefix[m + 1];
+    // matrix holding group g: last m with prefix[m] <= g (then walked forward)
+    auto locate = [&](long long g) {
+        int lo = 0, hi = nMat - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (groupPrefix[mid] <= g) lo = mid; else hi = mid - 1;
         }
-        const long long local = g - groupPrefix[m];
-        spmm_group_g32<VT, AT, K, V, VEC>(__ldg(d.gi + local), d.tm, d.cols,
-                                          static_cast<const VT *>(d.vals), X + d.colBase * K, K,
-                                          Y + d.rowBase * K, K, lane);
+        return lo;
+    };
+    auto bind = [&](GroupWork<VT, AT, K, V> &gw, long long g, int &m) {
+        while (g >= groupPrefix[m + 1]) ++m;
+        const BatchDesc &d = desc[m];
+        gw.info = __ldg(d.gi + (g - groupPrefix[m]));
+        gw.tm = d.tm;
+        gw.cols = d.cols;
+        gw.vals = static_cast<const VT *>(d.vals);
+        gw.X = X + d.colBase * K;
+        gw.Y = Y + d.rowBase * K;
+    };
+    // the first group of the pair runs over [gBegin, gEnd) by gStep; the
+    // second is `gap` groups behind it
+    long long gBegin, gEnd, gStep, gap;
+    if constexpr (STRIPED) {
+        gBegin = w; gEnd = totalGroups; gStep = 2 * W; gap = W;
+    } else {
+        const long long per = (totalGroups + W - 1) / W;
+        gBegin = w * per; gEnd = min(totalGroups, gBegin + per); gStep = 2; gap = 1;
+    }
+    if (gBegin >= gEnd) return;
+    int ma = locate(gBegin), mb = locate(min(gBegin + gap, totalGroups - 1));
+    GroupWork<VT, AT, K, V> a, b;
+    for (long long g = gBegin; g < gEnd; g += gStep) {
+        bind(a, g, ma);
+        if (g + gap < gEnd) {
+            bind(b, g + gap, mb);
+            a.issue(lane);
+            b.issue(lane);
+            a.finish(lane);
+            b.finish(lane);
+        } else {
+            a.issue(lane);
+            a.finish(lane);
+        }
     }
 }
 
@@ -273,27 +384,43 @@ argcsr_status launch_spmm_t(const argcsr_matrix *A, int k, const void *X, long l
     return ARGCSR_OK;
 }
 
-template <typename VT, typename AT, int K, bool VEC>
+// Grid of the batch kernel: twice the number of 256-thread blocks that fit
+// on all SMs at once.  Two waves of half-length runs balance better than one
+// wave (blocks that finish early make room for the second wave).
+template <typename Kern>
+unsigned persistent_grid(Kern kernel) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, 256, 0);
+    return (unsigned)(2 * max(sms, 1) * max(per, 1));
+}
+
+template <typename VT, typename AT, int K>
 void launch_batch_kv(const argcsr_batch *B, const void *X, void *Y, cudaStream_t s) {
-    const unsigned grid = 152u * 8u;   // persistent: 8 blocks of 8 warps per SM
+    constexpr bool S = K >= 4;
+    static const unsigned grids[3] = {persistent_grid(k_batch_spmm_g32<VT, AT, K, 1, S>),
+                                      persistent_grid(k_batch_spmm_g32<VT, AT, K, 2, S>),
+                                      persistent_grid(k_batch_spmm_g32<VT, AT, K, 4, S>)};
+    const unsigned grid = grids[B->V == 1 ? 0 : B->V == 2 ? 1 : 2];
     const auto *d = static_cast<const BatchDesc *>(B->d_desc);
     const auto *xx = static_cast<const AT *>(X);
     auto *yy = static_cast<AT *>(Y);
     switch (B->V) {
-        case 1: k_batch_spmm_g32<VT, AT, K, 1, VEC><<<grid, 256, 0, s>>>(d, B->d_groupPrefix, B->count, B->total_groups, xx, yy); break;
-        case 2: k_batch_spmm_g32<VT, AT, K, 2, VEC><<<grid, 256, 0, s>>>(d, B->d_groupPrefix, B->count, B->total_groups, xx, yy); break;
-        default: k_batch_spmm_g32<VT, AT, K, 4, VEC><<<grid, 256, 0, s>>>(d, B->d_groupPrefix, B->count, B->total_groups, xx, yy); break;
+        case 1: k_batch_spmm_g32<VT, AT, K, 1, S><<<grid, 256, 0, s>>>(d, B->d_groupPrefix, B->count, B->total_groups, xx, yy); break;
+        case 2: k_batch_spmm_g32<VT, AT, K, 2, S><<<grid, 256, 0, s>>>(d, B->d_groupPrefix, B->count, B->total_groups, xx, yy); break;
+        default: k_batch_spmm_g32<VT, AT, K, 4, S><<<grid, 256, 0, s>>>(d, B->d_groupPrefix, B->count, B->total_groups, xx, yy); break;
     }
 }
 
-template <typename VT, typename AT, bool VEC>
+template <typename VT, typename AT>
 argcsr_status launch_batch_t(const argcsr_batch *B, int k, const void *X, void *Y, cudaStream_t s) {
     switch (k) {
-        case 1: launch_batch_kv<VT, AT, 1, VEC>(B, X, Y, s); break;
-        case 2: launch_batch_kv<VT, AT, 2, VEC>(B, X, Y, s); break;
-        case 4: launch_batch_kv<VT, AT, 4, VEC>(B, X, Y, s); break;
-        case 8: launch_batch_kv<VT, AT, 8, VEC>(B, X, Y, s); break;
-        case 16: launch_batch_kv<VT, AT, 16, VEC>(B, X, Y, s); break;
+        case 1: launch_batch_kv<VT, AT, 1>(B, X, Y, s); break;
+        case 2: launch_batch_kv<VT, AT, 2>(B, X, Y, s); break;
+        case 4: launch_batch_kv<VT, AT, 4>(B, X, Y, s); break;
+        case 8: launch_batch_kv<VT, AT, 8>(B, X, Y, s); break;
+        case 16: launch_batch_kv<VT, AT, 16>(B, X, Y, s); break;
         default: return ARGCSR_ENOTSUP;
     }
     return ARGCSR_OK;
@@ -322,13 +449,12 @@ argcsr_status launch_spmm(const argcsr_matrix *A, int k, const void *X, long lon
 
 argcsr_status launch_batch(const argcsr_batch *B, int k, const void *X, void *Y, cudaStream_t s) {
     if (B->total_groups == 0) return ARGCSR_OK;
-    const bool vec = (uintptr_t)X % 16 == 0 && (uintptr_t)Y % 16 == 0;
     TraceScope t("k_batch_spmm_g32", s);
     argcsr_status st;
     switch (B->dtype) {
-        case ARGCSR_F64: st = vec ? launch_batch_t<double, double, true>(B, k, X, Y, s) : launch_batch_t<double, double, false>(B, k, X, Y, s); break;
-        case ARGCSR_F32: st = vec ? launch_batch_t<float, float, true>(B, k, X, Y, s) : launch_batch_t<float, float, false>(B, k, X, Y, s); break;
-        default: st = vec ? launch_batch_t<uint16_t, float, true>(B, k, X, Y, s) : launch_batch_t<uint16_t, float, false>(B, k, X, Y, s); break;
+        case ARGCSR_F64: st = launch_batch_t<double, double>(B, k, X, Y, s); break;
+        case ARGCSR_F32: st = launch_batch_t<float, float>(B, k, X, Y, s); break;
+        default: st = launch_batch_t<uint16_t, float>(B, k, X, Y, s); break;
     }
     if (st != ARGCSR_OK) return st;
     count_launches(1);
@@ -430,6 +556,7 @@ ARGCSR_API argcsr_status argcsr_batch_offsets(argcsr_batch_t B, int64_t *h_row_o
 ARGCSR_API argcsr_status argcsr_batch_spmm(argcsr_batch_t B, int32_t k, const void *d_X, void *d_Y,
                                            argcsr_stream_t stream) {
     if (!B || !valid_k(k) || !d_X || !d_Y) return ARGCSR_EINVAL;
+    if ((uintptr_t)d_X % 16 || (uintptr_t)d_Y % 16) return ARGCSR_EINVAL;   // vector access
     return launch_batch(B, k, d_X, d_Y, reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -437,7 +564,8 @@ ARGCSR_API argcsr_status argcsr_batch_graph_create(argcsr_batch_t B, int32_t k, 
                                                    void *d_Y, argcsr_graph_t *out) {
     if (!out) return ARGCSR_EINVAL;
     *out = nullptr;
-    if (!B || !valid_k(k) || !d_X || !d_Y) return ARGCSR_EINVAL;
+    if (!B || !valid_k(k) || !d_X || !d_Y || (uintptr_t)d_X % 16 || (uintptr_t)d_Y % 16)
+        return ARGCSR_EINVAL;
     cudaStream_t cs;
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e != cudaSuccess) return record_cuda(e, "cudaStreamCreateWithFlags");
@@ -544,6 +672,71 @@ ARGCSR_API argcsr_status argcsr_autotune(int32_t n_rows, int32_t n_cols, int64_t
             }
             argcsr_destroy(A, stream);
         }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    pool_free(X, s);
+    pool_free(Y, s);
+    if (st != ARGCSR_OK) return st;
+    *best = bp;
+    if (best_us) *best_us = bestT;
+    return ARGCSR_OK;
+}
+
+// Autotuning for a batch: every candidate desiredChunkSize converts all
+// `count` matrices (G = 32, V = 1) and times `reps` batch launches; the
+// fastest D is returned.  Matrix i is given by its own CSR device arrays.
+ARGCSR_API argcsr_status argcsr_autotune_batch(int32_t count, const int32_t *h_n_rows,
+                                               const int32_t *h_n_cols, const int64_t *h_nnz,
+                                               const int32_t *const *h_rowPointers,
+                                               const int32_t *const *h_columns,
+                                               const void *const *h_values, argcsr_dtype dtype,
+                                               int32_t k, int32_t reps, argcsr_stream_t stream,
+                                               argcsr_params *best, float *best_us) {
+    if (!best || count <= 0 || !valid_k(k) || reps < 1 || !h_n_rows || !h_n_cols || !h_nnz ||
+        !h_rowPointers || !h_columns || !h_values)
+        return ARGCSR_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int64_t rows = 0, cols = 0;
+    for (int i = 0; i < count; ++i) { rows += h_n_rows[i]; cols += h_n_cols[i]; }
+    const size_t es = vec_size(dtype);
+    void *X = nullptr, *Y = nullptr;
+    argcsr_status st = pool_alloc(&X, (size_t)cols * k * es, s);
+    if (st == ARGCSR_OK) st = pool_alloc(&Y, (size_t)rows * k * es, s);
+    if (st == ARGCSR_OK && X) cudaMemsetAsync(X, 0, (size_t)cols * k * es, s);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (st == ARGCSR_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        st = ARGCSR_ECUDA;
+    const int Ds[] = {1, 2, 4, 8, 16, 32};
+    float bestT = INFINITY;
+    argcsr_params bp{32, 1, 1};
+    std::vector<argcsr_t> mats(count, nullptr);
+    for (int D : Ds) {
+        if (st != ARGCSR_OK) break;
+        argcsr_params p{32, D, 1};
+        bool ok = true;
+        for (int i = 0; i < count && st == ARGCSR_OK; ++i) {
+            argcsr_status cs = argcsr_create_from_csr(h_n_rows[i], h_n_cols[i], h_nnz[i], h_rowPointers[i],
+                                                      h_columns[i], h_values[i], dtype, &p, stream, &mats[i]);
+            if (cs == ARGCSR_EOVERFLOW) { ok = false; break; }
+            if (cs != ARGCSR_OK) st = cs;
+        }
+        argcsr_batch_t B = nullptr;
+        if (st == ARGCSR_OK && ok) st = argcsr_batch_create(count, mats.data(), stream, &B);
+        if (st == ARGCSR_OK && ok) {
+            st = launch_batch(B, k, X, Y, s);   // warm-up
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < reps && st == ARGCSR_OK; ++r) st = launch_batch(B, k, X, Y, s);
+            cudaEventRecord(e1, s);
+            cudaError_t ee = cudaEventSynchronize(e1);
+            float ms = 0;
+            if (ee == cudaSuccess) ee = cudaEventElapsedTime(&ms, e0, e1);
+            if (ee != cudaSuccess && st == ARGCSR_OK) st = record_cuda(ee, "argcsr_autotune_batch timing");
+            const float us = ms * 1e3f / reps;
+            if (st == ARGCSR_OK && us < bestT) { bestT = us; bp = p; }
+        }
+        argcsr_batch_destroy(B, stream);
+        for (auto &A : mats) { argcsr_destroy(A, stream); A = nullptr; }
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);

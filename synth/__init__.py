@@ -25,7 +25,8 @@ import numpy as np
 
 __all__ = [
     "Csr", "laplacian_2d", "laplacian_3d", "lognormal_rows", "zipf_rows",
-    "banded", "block_diag", "random_csr", "spd_random", "fig3_example", "uniform_vector",
+    "banded", "block_diag", "random_csr", "spd_random", "diag_dominant", "diag_dominant_batch",
+    "fig3_example", "uniform_vector",
     "pathological_overflow_rowpointers", "workload",
 ]
 
@@ -115,33 +116,37 @@ def laplacian_3d(nx: int, ny: int | None = None, nz: int | None = None) -> Csr:
 
 def _distinct_sorted_columns(rng, lengths, n_cols):
     """Per row, ``lengths[r]`` distinct columns drawn uniformly from
-    [0, n_cols), sorted ascending.  Duplicates are redrawn until none remain."""
+    [0, n_cols), sorted ascending.  Rows using more than half of the columns
+    are drawn exactly without replacement; for the others, duplicates are
+    redrawn until none remain."""
     lengths = np.asarray(lengths, dtype=np.int64)
     n = lengths.size
     nnz = int(lengths.sum())
     if nnz == 0:
         return np.zeros(0, dtype=np.int32)
-    if n * n_cols <= 4_000_000 or lengths.max() * 4 > n_cols:
-        # small or dense rows: exact sampling without replacement per row
-        out = np.empty(nnz, dtype=np.int64)
-        p = 0
-        for r in range(n):
-            k = int(lengths[r])
-            if k:
-                out[p:p + k] = np.sort(rng.choice(n_cols, size=k, replace=False))
-                p += k
-        return out.astype(np.int32)
-    row_of = np.repeat(np.arange(n, dtype=np.int64), lengths)
-    cols = rng.integers(0, n_cols, size=nnz, dtype=np.int64)
-    while True:
-        key = row_of * n_cols + cols
-        order = np.argsort(key, kind="stable")
-        key = key[order]
-        cols = cols[order]
-        dup = np.flatnonzero(key[1:] == key[:-1]) + 1
-        if dup.size == 0:
-            return cols.astype(np.int32)
-        cols[dup] = rng.integers(0, n_cols, size=dup.size, dtype=np.int64)
+    rp = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(lengths, out=rp[1:])
+    out = np.empty(nnz, dtype=np.int64)
+    dense = np.flatnonzero(lengths * 2 > n_cols)
+    sparse = lengths * 2 <= n_cols
+    for r in dense:
+        out[rp[r]:rp[r + 1]] = np.sort(rng.choice(n_cols, size=int(lengths[r]), replace=False))
+    sl = lengths[sparse]
+    if sl.sum():
+        row_of = np.repeat(np.arange(sl.size, dtype=np.int64), sl)
+        cols = rng.integers(0, n_cols, size=int(sl.sum()), dtype=np.int64)
+        while True:
+            key = row_of * n_cols + cols
+            order = np.argsort(key, kind="stable")
+            key = key[order]
+            cols = cols[order]
+            dup = np.flatnonzero(key[1:] == key[:-1]) + 1
+            if dup.size == 0:
+                break
+            cols[dup] = rng.integers(0, n_cols, size=dup.size, dtype=np.int64)
+        mask = np.repeat(sparse, lengths)
+        out[mask] = cols
+    return out.astype(np.int32)
 
 
 def lognormal_rows(n: int, mu: float = 2.3, sigma: float = 1.2, max_len: int = 20000,
@@ -240,6 +245,53 @@ def spd_random(n: int, mean_len: float = 8.0, seed: int = 0, dtype=np.float64) -
     rows, cols, vals = rows[order], cols[order], vals[order]
     lengths = np.bincount(rows, minlength=n)
     return _from_lengths(n, n, lengths, cols, vals.astype(dtype), f"spd_random_{n}")
+
+
+def diag_dominant(n: int, rng, mu: float = 1.8, sigma: float = 1.0, max_len: int = 512,
+                  dtype=np.float32) -> Csr:
+    """Row lengths clip(rint(lognormal(mu, sigma)), 1, max_len) counting the
+    diagonal; off-diagonal columns uniform without replacement excluding the
+    row's own index, values N(0, 1); diagonal 1 + sum of |off-diagonals|
+    (strictly diagonally dominant)."""
+    lens = np.clip(np.rint(rng.lognormal(mu, sigma, n)), 1, min(max_len, n)).astype(np.int64)
+    off = lens - 1
+    oc = _distinct_sorted_columns(rng, off, max(n - 1, 1)).astype(np.int64)
+    orow = np.repeat(np.arange(n, dtype=np.int64), off)
+    oc += oc >= orow                                     # skip the diagonal column (stays sorted)
+    ov = rng.standard_normal(oc.size)
+    diag = 1.0 + np.bincount(orow, weights=np.abs(ov), minlength=n)
+    # place the diagonal among the row's sorted off-diagonal columns
+    rp = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(lens, out=rp[1:])
+    ro = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(off, out=ro[1:])
+    within = np.arange(oc.size, dtype=np.int64) - np.repeat(ro[:-1], off)
+    dest = np.repeat(rp[:-1], off) + within + (oc > orow)
+    below = np.bincount(orow[oc < orow], minlength=n)
+    cols = np.empty(int(rp[-1]), dtype=np.int64)
+    vals = np.empty(int(rp[-1]), dtype=np.float64)
+    cols[dest], vals[dest] = oc, ov
+    cols[rp[:-1] + below], vals[rp[:-1] + below] = np.arange(n), diag
+    return _from_lengths(n, n, lens, cols, vals.astype(dtype), f"diagdom_{n}")
+
+
+def _diag_dominant_member(args):
+    n, seed, m, dtype = args
+    return diag_dominant(n, np.random.default_rng([seed, m]), dtype=dtype)
+
+
+def diag_dominant_batch(count: int = 4096, n_min: int = 100, n_max: int = 20000, seed: int = 0,
+                        dtype=np.float32, workers: int = 1) -> list:
+    """``count`` independent matrices, n uniform in [n_min, n_max]; matrix m
+    is ``diag_dominant`` drawn from its own generator seeded (seed, m), so the
+    batch is the same whatever the number of worker processes."""
+    sizes = np.random.default_rng(seed).integers(n_min, n_max + 1, count)
+    jobs = [(int(n), seed, m, dtype) for m, n in enumerate(sizes)]
+    if workers <= 1:
+        return [_diag_dominant_member(j) for j in jobs]
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(_diag_dominant_member, jobs, chunksize=16)
 
 
 def fig3_example(dtype=np.float64) -> Csr:

@@ -742,6 +742,214 @@ def run_batched(args):
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# serving: SpMV and CG requests on a 64-matrix device-resident pool
+# ---------------------------------------------------------------------------
+
+SERVE_METRIC = ("served CG solves/s (80/20 SpMV/CG mix, tol 1e-8) and p50/p99 request latency "
+                "on a 64-matrix device-resident pool")
+
+
+def _pct(values, q):
+    return round(float(np.percentile(values, q)), 3) if len(values) else None
+
+
+def _latency_summary(kinds, lat_ms, makespan_s):
+    kinds = np.asarray(kinds)
+    lat_ms = np.asarray(lat_ms)
+    out = {"requests": int(kinds.size), "makespan_s": round(makespan_s, 4),
+           "requests_per_s": round(kinds.size / makespan_s, 2),
+           "cg_solves_per_s": round(int(np.sum(kinds == "cg")) / makespan_s, 2),
+           "p50_ms": _pct(lat_ms, 50), "p99_ms": _pct(lat_ms, 99)}
+    for k in ("spmv", "cg"):
+        sel = lat_ms[kinds == k]
+        out[f"{k}_p50_ms"], out[f"{k}_p99_ms"] = _pct(sel, 50), _pct(sel, 99)
+    return out
+
+
+def _sleep_until(t):
+    while True:
+        d = t - time.monotonic()
+        if d <= 0:
+            return
+        time.sleep(d if d > 2e-3 else 0)
+
+
+def run_serving(args):
+    import torch
+    from paper_1203_5737_gb300 import argcsr as api
+    from paper_1203_5737_gb300 import build
+    build.build()
+    t0 = time.time()
+    pool = synth.serving_pool(64, seed=0, workers=min(16, os.cpu_count() or 1))
+    gen_s = time.time() - t0
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream()
+    s = stream.cuda_stream
+    tol = 1e-8
+    mats = []
+    with torch.cuda.stream(stream):
+        for P in pool:
+            A = P["A"]
+            rp = torch.from_numpy(A.rowPointers).to(dev)
+            cols = torch.from_numpy(A.columns).to(dev)
+            v64 = torch.from_numpy(A.values).to(dev)
+            code = api.ARGCSR_F32 if P["storage"] == "f32" else api.ARGCSR_BF16
+            vs = v64.float() if code == api.ARGCSR_F32 else v64.bfloat16()
+            D = 8 if P["kind"].startswith("laplace") else 4
+            h = api.argcsr_create_from_csr(A.n_rows, A.n_cols, A.nnz, rp.data_ptr(), cols.data_ptr(),
+                                           vs.data_ptr(), code, GROUP_SIZE, D, 1, s)
+            # stencil values are exact in FP32/BF16; other members refine
+            # against their FP64 values
+            hr = None
+            if P["spd"] and not P["kind"].startswith("laplace"):
+                hr = api.argcsr_create_from_csr(A.n_rows, A.n_cols, A.nnz, rp.data_ptr(),
+                                                cols.data_ptr(), v64.data_ptr(), api.ARGCSR_F64,
+                                                GROUP_SIZE, D, 1, s)
+            stream.synchronize()
+            del vs
+            mats.append({"n": A.n_rows, "nnz": A.nnz, "kind": P["kind"], "spd": P["spd"],
+                         "storage": P["storage"], "h": h, "hr": hr, "rp": rp, "cols": cols, "v64": v64})
+    del pool
+    rng = np.random.default_rng(1)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1)
+    spd_ids = [i for i, M in enumerate(mats) if M["spd"]]
+    reqs = []
+    for _ in range(args.requests):
+        if rng.random() < 0.2:
+            i = int(rng.choice(spd_ids))
+            n = mats[i]["n"]
+            b = torch.rand(n, generator=gen, device=dev, dtype=torch.float64) * 2 - 1
+            reqs.append({"kind": "cg", "m": i, "b": b, "x": torch.zeros_like(b), "xb": torch.zeros_like(b)})
+        else:
+            i = int(rng.integers(len(mats)))
+            n = mats[i]["n"]
+            x64 = torch.rand(n, generator=gen, device=dev, dtype=torch.float64) * 2 - 1
+            reqs.append({"kind": "spmv", "m": i, "x64": x64, "x": x64.float(),
+                         "y": torch.empty(n, dtype=torch.float32, device=dev),
+                         "y64": torch.empty(n, dtype=torch.float64, device=dev)})
+    torch.cuda.synchronize()
+
+    def serve_ours(subset, offsets):
+        S = api.argcsr_server_create(hbm_budget_bytes=150 * 10**9, num_streams=args.serve_streams)
+        ids = [api.argcsr_server_add_matrix(S, M["h"], M["hr"]) for M in mats]
+        for q in subset:
+            if reqs[q]["kind"] == "cg":
+                reqs[q]["x"].zero_()
+        torch.cuda.synchronize()
+        l0 = api.argcsr_launch_count()
+        handles = []
+        start = time.monotonic()
+        for q, off in zip(subset, offsets):
+            _sleep_until(start + off)
+            r = reqs[q]
+            if r["kind"] == "cg":
+                handles.append(api.argcsr_server_submit_cg(S, ids[r["m"]], r["b"].data_ptr(),
+                                                           r["x"].data_ptr(), tol, 0))
+            else:
+                handles.append(api.argcsr_server_submit_spmv(S, ids[r["m"]], r["x"].data_ptr(),
+                                                             r["y"].data_ptr()))
+        api.argcsr_server_drain(S, 900.0)
+        infos = [api.argcsr_server_query(S, h) for h in handles]
+        api.argcsr_server_destroy(S)
+        launches = api.argcsr_launch_count() - l0
+        t_sub = np.array([i["t_submit_us"] for i in infos])
+        t_done = np.array([i["t_done_us"] for i in infos])
+        summ = _latency_summary([reqs[q]["kind"] for q in subset], (t_done - t_sub) / 1e3,
+                                (t_done.max() - t_sub.min()) / 1e6)
+        cg = [i for q, i in zip(subset, infos) if reqs[q]["kind"] == "cg"]
+        batches = [i["batch"] for q, i in zip(subset, infos) if reqs[q]["kind"] == "spmv"]
+        lag = t_sub / 1e6 - (start + np.asarray(offsets))
+        summ.update({"failed": int(sum(i["state"] != 2 for i in infos)),
+                     "cg_converged": int(sum(i["converged"] for i in cg)),
+                     "cg_max_rel_residual": max((i["rel_residual"] for i in cg), default=None),
+                     "cg_mean_inner_iters": round(float(np.mean([i["iters"] for i in cg])), 1) if cg else None,
+                     "spmv_mean_batch": round(float(np.mean(batches)), 3) if batches else None,
+                     "client_max_lag_ms": round(float(lag.max()) * 1e3, 3),
+                     "gpu_launches": int(launches)})
+        return summ
+
+    def serve_baseline(subset, offsets):
+        """Plain FP64 CSR (the library's vector CSR SpMV and CG) served
+        first-come first-served, one request at a time."""
+        for q in subset:
+            if reqs[q]["kind"] == "cg":
+                reqs[q]["xb"].zero_()
+        torch.cuda.synchronize()
+        lat, kinds, cg_conv = [], [], 0
+        start = time.monotonic()
+        for q, off in zip(subset, offsets):
+            arrival = start + off
+            _sleep_until(arrival)
+            r = reqs[q]
+            M = mats[r["m"]]
+            if r["kind"] == "cg":
+                res = api.argcsr_baseline_csr_cg(M["n"], M["nnz"], M["rp"].data_ptr(), M["cols"].data_ptr(),
+                                                 M["v64"].data_ptr(), r["b"].data_ptr(), r["xb"].data_ptr(),
+                                                 tol=tol, stream=s)
+                cg_conv += res["converged"]
+            else:
+                api.argcsr_baseline_csr_spmv(M["n"], M["n"], M["nnz"], M["rp"].data_ptr(),
+                                             M["cols"].data_ptr(), M["v64"].data_ptr(), api.ARGCSR_F64, 1,
+                                             r["x64"].data_ptr(), r["y64"].data_ptr(), s)
+                stream.synchronize()
+            lat.append((time.monotonic() - arrival) * 1e3)
+            kinds.append(r["kind"])
+        makespan = time.monotonic() - start
+        summ = _latency_summary(kinds, lat, makespan)
+        summ["cg_converged"] = int(cg_conv)
+        return summ
+
+    everything = list(range(len(reqs)))
+    warm = everything[: min(64, len(reqs))]
+    serve_ours(warm, [0.0] * len(warm))
+    serve_baseline(warm, [0.0] * len(warm))
+    clocks = ClockSampler(0)
+    clocks.start()
+    sat = serve_ours(everything, [0.0] * len(everything))
+    clock_info = clocks.stop()
+    sat_base = serve_baseline(everything, [0.0] * len(everything))
+    # Poisson arrivals at fractions of the saturated request rate
+    loads = []
+    half = everything[: max(1, len(everything) // 2)]
+    for frac in (0.25, 0.5, 0.75):
+        rate = frac * sat["requests_per_s"]
+        gaps = np.random.default_rng(int(frac * 100)).exponential(1.0 / rate, len(half))
+        offsets = list(np.cumsum(gaps) - gaps[0])
+        loads.append({"offered_requests_per_s": round(rate, 2), "fraction_of_saturation": frac,
+                      "argcsr_server": serve_ours(half, offsets),
+                      "plain_csr_f64_fifo": serve_baseline(half, offsets)})
+    total_nnz = int(sum(M["nnz"] for M in mats))
+    kinds = {}
+    for M in mats:
+        kinds.setdefault(M["kind"], [0, 0])
+        kinds[M["kind"]][0] += 1
+        kinds[M["kind"]][1] += M["nnz"]
+    out = {"metric": SERVE_METRIC, "unit": "solves/s", "higher_is_better": True, "n_gpus": 1,
+           "value": sat["cg_solves_per_s"], "dtype": "f32/bf16 storage, f32 inner CG, f64 refinement",
+           "data": "synthetic", "vs_baseline": None,
+           "config": {"workload": "64 matrices, n log-uniform in [1e4, 2e6] (Zipf members at most 5e4 "
+                                  "rows): 2D/3D Laplacians, symmetrised lognormal(1.8, 1.0) "
+                                  "diagonally dominant (SPD), Zipf(1.5) rows up to 50 000 entries "
+                                  "(SpMV only); FP32/BF16 alternating; requests 80% SpMV / 20% CG "
+                                  "(SPD members, tol 1e-8), x, b ~ U[-1,1]; HBM budget 150 GB",
+                      "requests": len(reqs), "streams": args.serve_streams,
+                      "pool_total_nnz": total_nnz,
+                      "pool_kinds": {k: {"matrices": v[0], "nnz": v[1]} for k, v in kinds.items()},
+                      "pool_generation_s": round(gen_s, 1)},
+           "saturation": {"argcsr_server": sat, "plain_csr_f64_fifo": sat_base},
+           "poisson": loads, "clocks": clock_info,
+           "gpu_launches": sat["gpu_launches"]}
+    print(json.dumps(out), flush=True)
+    for M in mats:
+        api.argcsr_destroy(M["h"], s)
+        if M["hr"] is not None:
+            api.argcsr_destroy(M["hr"], s)
+    stream.synchronize()
+
+
 def run_ncu_case(which):
     """A short, untimed launch sequence for ncu captures: for each matrix, one
     conversion (k_tile_prepare, k_resolve, k_groups, k_tile_scan, k_fill) and
@@ -783,12 +991,15 @@ def main(argv=None):
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--ncu-case", choices=("small", "bench"),
                    help="run a short untimed launch sequence for ncu, then exit")
-    p.add_argument("--workload", choices=("uneven_fp64", "cg_poisson160", "batched4096"),
+    p.add_argument("--workload", choices=("uneven_fp64", "cg_poisson160", "batched4096", "serving"),
                    default="uneven_fp64",
                    help="uneven_fp64: the conversion + SpMV step (default); cg_poisson160: "
                         "mixed-precision CG with FP64 refinement; batched4096: multi-RHS "
-                        "products of 4096 matrices in one graph launch")
+                        "products of 4096 matrices in one graph launch; serving: SpMV and "
+                        "CG requests on a 64-matrix pool through the serving engine")
     p.add_argument("--batch-count", type=int, default=4096)
+    p.add_argument("--requests", type=int, default=600, help="serving: requests per saturation run")
+    p.add_argument("--serve-streams", type=int, default=16, help="serving: stream slots")
     args = p.parse_args(argv)
     if args.ncu_case:
         run_ncu_case(args.ncu_case)
@@ -798,6 +1009,9 @@ def main(argv=None):
         return
     if args.workload == "batched4096":
         run_batched(args)
+        return
+    if args.workload == "serving":
+        run_serving(args)
         return
     args.warmup = max(3, args.warmup)   # at least three untimed warm-up steps
     if args.impl == "reference":

@@ -296,6 +296,78 @@ ARGCSR_API argcsr_status argcsr_baseline_csr_cg(int32_t n, int64_t nnz, const in
                                                 argcsr_stream_t stream, argcsr_cg_result *result);
 
 /* ---------------------------------------------------------------------------
+ * Serving: SpMV and CG-solve requests on a pool of device-resident matrices
+ * with continuous batching (a library runtime; the paper has no serving
+ * layer).  A worker thread owns the GPU side.  Oldest first, it admits
+ * requests while a stream slot (num_streams, max_inflight) and HBM budget
+ * are free; CG jobs leave spmv_streams slots to SpMV, and SpMV requests
+ * pass CG requests that wait for a slot or for memory:
+ *   - SpMV requests on the same matrix are fused, up to max_batch of them,
+ *     into one SpMM launch; their x vectors become the columns of X.
+ *   - A CG request becomes a resumable job on its own stream.
+ * Work admitted while other requests run overlaps with them on the device.
+ *
+ * Budget: matrices count toward hbm_budget_bytes when added.  Each request
+ * also counts while it runs: its work arrays are packed X/Y for fused SpMV,
+ * and 4 vectors of the working type + 1 FP64 vector for CG.  A request that
+ * cannot fit even on an idle server fails with ARGCSR_ENOMEM.
+ *
+ * Request buffers are device pointers owned by the caller, kept alive until
+ * the request is done:
+ *   - SpMV: d_x (n_cols) in, d_y (n_rows) out; f64 for ARGCSR_F64 matrices,
+ *     f32 otherwise.
+ *   - CG: d_b in, d_x in (initial guess) / out; both f64.  Tolerance as in
+ *     argcsr_cg_solve.
+ *
+ * Register every matrix before the first request (later: ARGCSR_EINVAL).
+ * Matrices are borrowed
+ * and must outlive the server.  argcsr_server_destroy serves what is queued,
+ * then stops.  Times are host microseconds (a monotonic clock).
+ * ------------------------------------------------------------------------ */
+typedef struct argcsr_server *argcsr_server_t;
+typedef struct {
+    int64_t hbm_budget_bytes;  /* 0: no limit                                   */
+    int32_t max_inflight;      /* requests on the GPU at once; 0: 64            */
+    int32_t num_streams;       /* stream slots; 0: 8                            */
+    int32_t max_batch;         /* SpMV requests per fused launch (<= 16); 0: 16 */
+    int32_t cg_check_every;    /* inner CG iterations per job step; 0: 16       */
+    int32_t spmv_streams;      /* slots CG jobs leave to SpMV, below num_streams;
+                                  0: num_streams / 4 (1 for 2 or 3 streams,
+                                  none for 1)                                   */
+} argcsr_server_params;
+
+typedef struct {
+    int32_t state;             /* 0 queued, 1 running, 2 done, 3 failed         */
+    int32_t status;            /* argcsr_status of the request                  */
+    int32_t iters;             /* CG: inner iterations                          */
+    int32_t batch;             /* requests fused with this one (SpMV)           */
+    int32_t converged;         /* CG: reached the tolerance                     */
+    int32_t reserved;
+    double t_submit_us, t_start_us, t_done_us;
+    double rel_residual;       /* CG: ||b - A x|| / ||b|| at the end            */
+} argcsr_request_info;
+
+ARGCSR_API argcsr_status argcsr_server_create(const argcsr_server_params *params, argcsr_server_t *out);
+ARGCSR_API argcsr_status argcsr_server_add_matrix(argcsr_server_t server, argcsr_t A,
+                                                  argcsr_t A_residual, int32_t *id);
+ARGCSR_API argcsr_status argcsr_server_submit_spmv(argcsr_server_t server, int32_t matrix,
+                                                   const void *d_x, void *d_y, int64_t *request);
+ARGCSR_API argcsr_status argcsr_server_submit_cg(argcsr_server_t server, int32_t matrix,
+                                                 const double *d_b, double *d_x, double tol,
+                                                 int32_t max_iters, int64_t *request);
+ARGCSR_API argcsr_status argcsr_server_query(argcsr_server_t server, int64_t request,
+                                             argcsr_request_info *info);
+/* Wait for one request (timeout_s <= 0: no limit); ARGCSR_ENOTSUP on timeout. */
+ARGCSR_API argcsr_status argcsr_server_wait(argcsr_server_t server, int64_t request,
+                                            double timeout_s, argcsr_request_info *info);
+/* Wait until every submitted request is done; ARGCSR_ENOTSUP on timeout. */
+ARGCSR_API argcsr_status argcsr_server_drain(argcsr_server_t server, double timeout_s);
+ARGCSR_API argcsr_status argcsr_server_stats(argcsr_server_t server, int64_t *matrix_bytes,
+                                             int64_t *work_bytes, int64_t *pending,
+                                             int64_t *unfinished);
+ARGCSR_API argcsr_status argcsr_server_destroy(argcsr_server_t server);
+
+/* ---------------------------------------------------------------------------
  * argcsr_convert_noalloc -- the CSR -> ARG-CSR conversion of
  * argcsr_create_from_csr for callers that cannot allocate device memory.
  * The paper has no counterpart; this is a library facility.

@@ -52,6 +52,22 @@ class argcsr_cg_result(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class argcsr_server_params(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int32),
+                ("num_streams", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("cg_check_every", ctypes.c_int32), ("spmv_streams", ctypes.c_int32)]
+
+
+class argcsr_request_info(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32), ("iters", ctypes.c_int32),
+                ("batch", ctypes.c_int32), ("converged", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("t_submit_us", ctypes.c_double), ("t_start_us", ctypes.c_double),
+                ("t_done_us", ctypes.c_double), ("rel_residual", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
 class ArgcsrError(RuntimeError):
     def __init__(self, status, where):
         msg = f"{where}: {argcsr_status_string(status)}"
@@ -106,6 +122,16 @@ _SIGNATURES = {
     "argcsr_autotune_batch": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P, _P, ctypes.c_int, _I32, _I32,
                                              _P, ctypes.POINTER(argcsr_params),
                                              ctypes.POINTER(ctypes.c_float)]),
+    "argcsr_server_create": (ctypes.c_int, [ctypes.POINTER(argcsr_server_params), ctypes.POINTER(_P)]),
+    "argcsr_server_add_matrix": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(_I32)]),
+    "argcsr_server_submit_spmv": (ctypes.c_int, [_P, _I32, _P, _P, ctypes.POINTER(_I64)]),
+    "argcsr_server_submit_cg": (ctypes.c_int, [_P, _I32, _P, _P, ctypes.c_double, _I32,
+                                               ctypes.POINTER(_I64)]),
+    "argcsr_server_query": (ctypes.c_int, [_P, _I64, ctypes.POINTER(argcsr_request_info)]),
+    "argcsr_server_wait": (ctypes.c_int, [_P, _I64, ctypes.c_double, ctypes.POINTER(argcsr_request_info)]),
+    "argcsr_server_drain": (ctypes.c_int, [_P, ctypes.c_double]),
+    "argcsr_server_stats": (ctypes.c_int, [_P] + [ctypes.POINTER(_I64)] * 4),
+    "argcsr_server_destroy": (ctypes.c_int, [_P]),
     "argcsr_trace_begin": (ctypes.c_int, []),
     "argcsr_trace_end": (ctypes.c_int, []),
     "argcsr_trace_kernel_count": (ctypes.c_int32, []),
@@ -320,6 +346,65 @@ def argcsr_autotune_batch(n_rows, n_cols, nnz, rp_ptrs, col_ptrs, val_ptrs, dtyp
     return (best.group_size, best.desired_chunk_size, best.vec_width), us.value
 
 
+def argcsr_server_create(hbm_budget_bytes=0, max_inflight=0, num_streams=0, max_batch=0,
+                         cg_check_every=0, spmv_streams=0) -> int:
+    p = argcsr_server_params(hbm_budget_bytes, max_inflight, num_streams, max_batch,
+                             cg_check_every, spmv_streams)
+    out = ctypes.c_void_p()
+    _check(load_library().argcsr_server_create(ctypes.byref(p), ctypes.byref(out)),
+           "argcsr_server_create")
+    return out.value
+
+
+def argcsr_server_add_matrix(S, A, A_residual=None) -> int:
+    i = ctypes.c_int32()
+    _check(load_library().argcsr_server_add_matrix(S, A, A_residual, ctypes.byref(i)),
+           "argcsr_server_add_matrix")
+    return i.value
+
+
+def argcsr_server_submit_spmv(S, matrix, d_x, d_y) -> int:
+    r = ctypes.c_int64()
+    _check(load_library().argcsr_server_submit_spmv(S, matrix, d_x, d_y, ctypes.byref(r)),
+           "argcsr_server_submit_spmv")
+    return r.value
+
+
+def argcsr_server_submit_cg(S, matrix, d_b, d_x, tol=1e-8, max_iters=0) -> int:
+    r = ctypes.c_int64()
+    _check(load_library().argcsr_server_submit_cg(S, matrix, d_b, d_x, tol, max_iters,
+                                                  ctypes.byref(r)), "argcsr_server_submit_cg")
+    return r.value
+
+
+def argcsr_server_query(S, request) -> dict:
+    info = argcsr_request_info()
+    _check(load_library().argcsr_server_query(S, request, ctypes.byref(info)), "argcsr_server_query")
+    return info.as_dict()
+
+
+def argcsr_server_wait(S, request, timeout_s=0.0) -> dict:
+    info = argcsr_request_info()
+    _check(load_library().argcsr_server_wait(S, request, timeout_s, ctypes.byref(info)),
+           "argcsr_server_wait")
+    return info.as_dict()
+
+
+def argcsr_server_drain(S, timeout_s=0.0) -> None:
+    _check(load_library().argcsr_server_drain(S, timeout_s), "argcsr_server_drain")
+
+
+def argcsr_server_stats(S) -> dict:
+    vals = [ctypes.c_int64() for _ in range(4)]
+    _check(load_library().argcsr_server_stats(S, *[ctypes.byref(v) for v in vals]),
+           "argcsr_server_stats")
+    return dict(zip(("matrix_bytes", "work_bytes", "pending", "unfinished"), (v.value for v in vals)))
+
+
+def argcsr_server_destroy(S) -> None:
+    _check(load_library().argcsr_server_destroy(S), "argcsr_server_destroy")
+
+
 def argcsr_residual(A, d_b, d_x, d_r, stream=0) -> None:
     _check(load_library().argcsr_residual(A, d_b, d_x, d_r, stream), "argcsr_residual")
 
@@ -530,3 +615,70 @@ def baseline_csr_spmv(rowPointers, columns, values, n_cols, x, variant=1, out=No
     argcsr_baseline_csr_spmv(n_rows, n_cols, columns.numel(), _ptr(rowPointers), _ptr(columns),
                              _ptr(values), code, variant, _ptr(x), _ptr(out), _stream(stream))
     return out
+
+
+class ArgCsrServer:
+    """Continuous-batching server over device-resident matrices (thin
+    wrapper of the argcsr_server_* calls).  It keeps each request's tensors
+    alive until the request has been waited for."""
+
+    def __init__(self, hbm_budget_bytes=0, max_inflight=0, num_streams=0, max_batch=0,
+                 cg_check_every=0, spmv_streams=0):
+        self._h = argcsr_server_create(hbm_budget_bytes, max_inflight, num_streams, max_batch,
+                                       cg_check_every, spmv_streams)
+        self._mats = []
+        self._live = {}
+
+    def add_matrix(self, A, A_residual=None) -> int:
+        i = argcsr_server_add_matrix(self._h, A.handle,
+                                     A_residual.handle if A_residual is not None else None)
+        self._mats.append((A, A_residual))
+        return i
+
+    def submit_spmv(self, matrix, x, y) -> int:
+        A = self._mats[matrix][0]
+        _check_cuda("x", x, A.vector_dtype)
+        _check_cuda("y", y, A.vector_dtype)
+        if x.numel() != A.n_cols or y.numel() != A.n_rows:
+            raise ValueError("x or y has the wrong length")
+        r = argcsr_server_submit_spmv(self._h, matrix, _ptr(x), _ptr(y))
+        self._live[r] = (x, y)
+        return r
+
+    def submit_cg(self, matrix, b, x, tol=1e-8, max_iters=0) -> int:
+        torch = _torch()
+        A = self._mats[matrix][0]
+        _check_cuda("b", b, torch.float64)
+        _check_cuda("x", x, torch.float64)
+        if b.numel() != A.n_rows or x.numel() != A.n_cols:
+            raise ValueError("b or x has the wrong length")
+        r = argcsr_server_submit_cg(self._h, matrix, _ptr(b), _ptr(x), tol, max_iters)
+        self._live[r] = (b, x)
+        return r
+
+    def query(self, request) -> dict:
+        return argcsr_server_query(self._h, request)
+
+    def wait(self, request, timeout_s=0.0) -> dict:
+        info = argcsr_server_wait(self._h, request, timeout_s)
+        self._live.pop(request, None)
+        return info
+
+    def drain(self, timeout_s=0.0) -> None:
+        argcsr_server_drain(self._h, timeout_s)
+        self._live.clear()
+
+    def stats(self) -> dict:
+        return argcsr_server_stats(self._h)
+
+    def close(self):
+        if self._h is not None:
+            argcsr_server_destroy(self._h)
+            self._h = None
+            self._live.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

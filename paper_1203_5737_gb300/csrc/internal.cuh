@@ -51,6 +51,7 @@ inline void count_launches(uint64_t k = 1) { g_launches.fetch_add(k, std::memory
 // Tracing: while argcsr_trace_begin() is in effect, a TraceScope records an
 // event pair around the launches made during its lifetime.
 int trace_start(const char *name, cudaStream_t s);
+bool trace_active();
 void trace_stop(int token, cudaStream_t s);
 struct TraceScope {
     int token;
@@ -89,6 +90,29 @@ argcsr_status launch_csr_residual_f64(int32_t n, int32_t n_cols, int64_t nnz, co
 // (stored values are widened exactly).
 argcsr_status launch_residual_f64(const argcsr_matrix *A, const double *b, const double *x,
                                   double *r, cudaStream_t s);
+
+// A conjugate-gradient solve as a resumable job (solver.cu): start() and
+// advance() enqueue work on the job's stream and return at once; a step is
+// complete when step_done() (or wait_step() returns).
+class CgJob {
+public:
+    virtual ~CgJob() = default;
+    virtual argcsr_status start() = 0;
+    virtual argcsr_status advance() = 0;
+    virtual bool step_done() const = 0;
+    virtual argcsr_status wait_step() = 0;
+    virtual bool finished() const = 0;
+    virtual argcsr_status status() const = 0;
+    virtual void result(argcsr_cg_result *r) const = 0;
+    virtual size_t workspace_bytes() const = 0;
+};
+CgJob *make_cg_job(const argcsr_matrix *A, const argcsr_matrix *Ares, const double *b, double *x,
+                   const argcsr_cg_params &P, cudaStream_t s);
+size_t cg_job_bytes(const argcsr_matrix *A);
+
+// SpMM launch (spmm.cu), for the serving engine.
+argcsr_status launch_spmm_public(const argcsr_matrix *A, int k, const void *X, long long ldx, void *Y,
+                                 long long ldy, cudaStream_t s);
 
 }  // namespace argcsr
 

@@ -18,14 +18,26 @@
 // iterations to decide convergence.
 #include <math.h>
 
+#include <mutex>
+#include <new>
+#include <vector>
+
 #include "internal.cuh"
 
 namespace argcsr {
 namespace {
 
-constexpr int kVecBlocks = 152 * 8;  // grid of the vector kernels (= number of partials)
+constexpr int kVecBlocks = 152 * 8;  // largest grid of the vector kernels (= partials)
 constexpr int kUnroll = 4;           // independent elements per thread per step
 constexpr int kVecThreads = 256;
+
+// Grid of the vector kernels for n elements: one block per kUnroll * 256
+// elements, at most kVecBlocks.  Small solves then occupy few SMs, so that
+// the serving engine's concurrent jobs really run side by side.
+inline int vec_blocks(long long n) {
+    const long long b = (n + (long long)kUnroll * kVecThreads - 1) / ((long long)kUnroll * kVecThreads);
+    return (int)(b < 1 ? 1 : b > kVecBlocks ? kVecBlocks : b);
+}
 
 // Device-resident scalars of a solve.
 struct CgState {
@@ -195,118 +207,253 @@ struct Operator {
     }
 };
 
-template <typename WT>
-struct Workspace {
-    WT *r = nullptr, *p = nullptr, *q = nullptr, *d = nullptr;
-    double *r64 = nullptr, *partials = nullptr;
-    CgState *S = nullptr;
-    CgState hS[1];           // host copy read at convergence checks
-    cudaStream_t s;
-    ~Workspace() {
-        pool_free(r, s); pool_free(p, s); pool_free(q, s); pool_free(d, s);
-        pool_free(r64, s); pool_free(partials, s); pool_free(S, s);
+// Pinned host copies of the solver state, reused across solves.
+std::mutex g_pinned_mu;
+std::vector<CgState *> g_pinned_free;
+
+CgState *take_pinned() {
+    {
+        std::lock_guard<std::mutex> lock(g_pinned_mu);
+        if (!g_pinned_free.empty()) {
+            CgState *p = g_pinned_free.back();
+            g_pinned_free.pop_back();
+            return p;
+        }
     }
+    CgState *p = nullptr;
+    if (cudaHostAlloc((void **)&p, sizeof(CgState), cudaHostAllocDefault) != cudaSuccess) return nullptr;
+    return p;
+}
+
+void give_pinned(CgState *p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lock(g_pinned_mu);
+    g_pinned_free.push_back(p);
+}
+
+// One solve as a resumable state machine: every call to advance() enqueues
+// the next block of work on the job's stream (ending with an asynchronous
+// copy of the device state to pinned host memory and an event) and returns
+// at once; when the event has completed, the next advance() reads the copy
+// and decides.  A synchronous solve loops on the event; the serving engine
+// interleaves many jobs on their own streams.
+template <typename WT>
+class CgJobT final : public CgJob {
+public:
+    CgJobT(const Operator &op, long long n, const double *b, double *x, const argcsr_cg_params &P,
+           cudaStream_t s)
+        : op_(op), n_(n), b_(b), x_(x), P_(P), s_(s), blocks_(vec_blocks(n)) {}
+
+    ~CgJobT() override {
+        pool_free(r_, s_); pool_free(p_, s_); pool_free(q_, s_); pool_free(d_, s_);
+        pool_free(r64_, s_); pool_free(partials_, s_); pool_free(S_, s_);
+        if (ev_) cudaEventDestroy(ev_);
+        if (inner_exec_) cudaGraphExecDestroy(inner_exec_);
+        give_pinned(hS_);
+    }
+
+    size_t workspace_bytes() const override { return bytes_for(n_); }
+    static size_t bytes_for(long long n) {
+        return 4 * (size_t)n * sizeof(WT) + (size_t)n * 8 + (size_t)kVecBlocks * 8 + sizeof(CgState) + 7 * 256;
+    }
+
+    argcsr_status start() override {
+        const size_t vb = (size_t)n_ * sizeof(WT);
+        argcsr_status st;
+        if ((st = pool_alloc((void **)&r_, vb, s_)) || (st = pool_alloc((void **)&p_, vb, s_)) ||
+            (st = pool_alloc((void **)&q_, vb, s_)) || (st = pool_alloc((void **)&d_, vb, s_)) ||
+            (st = pool_alloc((void **)&r64_, (size_t)n_ * 8, s_)) ||
+            (st = pool_alloc((void **)&partials_, (size_t)kVecBlocks * 8, s_)) ||
+            (st = pool_alloc((void **)&S_, sizeof(CgState), s_)))
+            return fail(st);
+        hS_ = take_pinned();
+        if (!hS_) return fail(ARGCSR_ENOMEM);
+        cudaError_t e = cudaEventCreateWithFlags(&ev_, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMemsetAsync(S_, 0, sizeof(CgState), s_);
+        if (e != cudaSuccess) return fail(record_cuda(e, "cg job start"));
+        inner_tol_ = P_.inner_tol > 0 ? P_.inner_tol : (sizeof(WT) == 4 ? 1e-5 : P_.tol);
+        check_ = P_.check_every > 0 ? P_.check_every : 16;
+        // Graph replay needs a stream that can be captured (not the legacy
+        // default stream, not synchronising with it) and no kernel tracing
+        // (a replayed graph records no trace events).
+        unsigned flags = 0;
+        graph_ok_ = s_ != nullptr && s_ != cudaStreamLegacy && s_ != cudaStreamPerThread &&
+                    cudaStreamGetFlags(s_, &flags) == cudaSuccess && (flags & cudaStreamNonBlocking) &&
+                    !trace_active();
+        {
+            TraceScope t("k_norm2_f64", s_);
+            k_norm2_f64<<<blocks_, kVecThreads, 0, s_>>>(b_, n_, partials_, S_, 1);
+        }
+        count_launches(1);
+        return enqueue_residual();
+    }
+
+    argcsr_status advance() override {
+        if (phase_ == Done || phase_ == Failed) return status_;
+        const CgState &h = *hS_;
+        if (phase_ == OuterCheck) {
+            const double bn = sqrt(h.bnorm2);
+            rel_ = bn > 0 ? sqrt(h.norm2) / bn : sqrt(h.norm2);
+            if (rel_ <= P_.tol) { converged_ = true; phase_ = Done; return ARGCSR_OK; }
+            if (outer_ >= P_.max_outer || inner_total_ >= P_.max_iters) { phase_ = Done; return ARGCSR_OK; }
+            ++outer_;
+            // reduce the inner residual by what is still missing (4x
+            // margin), but not below what the working precision can reach
+            const double need = rel_ > 0 ? 0.25 * P_.tol / rel_ : inner_tol_;
+            const double step_tol = need > inner_tol_ ? need : inner_tol_;
+            target_ = step_tol * step_tol;
+            {
+                TraceScope t("k_ir_start", s_);
+                k_ir_start<WT><<<blocks_, kVecThreads, 0, s_>>>(r64_, r_, p_, d_, n_, partials_, S_);
+            }
+            count_launches(1);
+            return enqueue_inner();
+        }
+        // InnerCheck
+        if (h.rho > target_ * h.rho0 && inner_total_ < P_.max_iters) return enqueue_inner();
+        {
+            TraceScope t("k_ir_correct", s_);
+            k_ir_correct<WT><<<blocks_, kVecThreads, 0, s_>>>(x_, d_, n_, S_);
+        }
+        count_launches(1);
+        return enqueue_residual();
+    }
+
+    bool step_done() const override { return ev_ && cudaEventQuery(ev_) != cudaErrorNotReady; }
+    argcsr_status wait_step() override {
+        cudaError_t e = cudaEventSynchronize(ev_);
+        return e == cudaSuccess ? ARGCSR_OK : fail(record_cuda(e, "cg job wait"));
+    }
+    bool finished() const override { return phase_ == Done || phase_ == Failed; }
+    argcsr_status status() const override { return status_; }
+    void result(argcsr_cg_result *r) const override {
+        r->outer_iters = outer_;
+        r->inner_iters = inner_total_;
+        r->converged = converged_ ? 1 : 0;
+        r->reserved = 0;
+        r->rel_residual = rel_;
+    }
+
+private:
+    enum Phase { OuterCheck, InnerCheck, Done, Failed };
+
+    argcsr_status fail(argcsr_status st) {
+        phase_ = Failed;
+        status_ = st;
+        return st;
+    }
+
+    // r = b - A x, ||r||^2, then read the state
+    argcsr_status enqueue_residual() {
+        argcsr_status st = op_.residual(b_, x_, r64_, s_);
+        if (st != ARGCSR_OK) return fail(st);
+        {
+            TraceScope t("k_norm2_f64", s_);
+            k_norm2_f64<<<blocks_, kVecThreads, 0, s_>>>(r64_, n_, partials_, S_, 0);
+        }
+        count_launches(1);
+        phase_ = OuterCheck;
+        return enqueue_readback();
+    }
+
+    // `check` inner CG iterations, then read the state
+    argcsr_status enqueue_inner() {
+        if (!inner_exec_ && trace_active()) graph_ok_ = false;   // keep traced launches visible
+        argcsr_status st = graph_ok_ ? launch_inner_graph() : launch_inner();
+        if (st != ARGCSR_OK) return fail(st);
+        inner_total_ += check_;
+        phase_ = InnerCheck;
+        return enqueue_readback();
+    }
+
+    // The inner step is the same launch sequence every time: capture it
+    // once into a graph and replay it (one launch instead of 4 per
+    // iteration, which is what bounds small solves).
+    argcsr_status launch_inner_graph() {
+        if (!inner_exec_) {
+            cudaError_t e = cudaStreamBeginCapture(s_, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return record_cuda(e, "cg step capture");
+            argcsr_status st = launch_inner();
+            cudaGraph_t g = nullptr;
+            e = cudaStreamEndCapture(s_, &g);
+            if (st == ARGCSR_OK && e != cudaSuccess) st = record_cuda(e, "cg step capture");
+            if (st == ARGCSR_OK) {
+                e = cudaGraphInstantiate(&inner_exec_, g, 0);
+                if (e != cudaSuccess) {
+                    inner_exec_ = nullptr;
+                    st = record_cuda(e, "cg step instantiate");
+                }
+            }
+            if (g) cudaGraphDestroy(g);
+            // the capture counted the kernels without running them
+            g_launches.fetch_sub(kernels_per_step(), std::memory_order_relaxed);
+            if (st != ARGCSR_OK) return st;
+        }
+        cudaError_t e = cudaGraphLaunch(inner_exec_, s_);
+        if (e != cudaSuccess) return record_cuda(e, "cg step launch");
+        count_launches(kernels_per_step());
+        return ARGCSR_OK;
+    }
+    uint64_t kernels_per_step() const { return 4ull * (uint64_t)check_; }
+
+    argcsr_status launch_inner() {
+        for (int k = 0; k < check_; ++k) {
+            argcsr_status st = op_.apply(p_, q_, s_);
+            if (st != ARGCSR_OK) return st;
+            {
+                TraceScope t("k_cg_alpha", s_);
+                k_cg_alpha<WT><<<blocks_, kVecThreads, 0, s_>>>(p_, q_, n_, partials_, S_);
+            }
+            {
+                TraceScope t("k_cg_update", s_);
+                k_cg_update<WT><<<blocks_, kVecThreads, 0, s_>>>(d_, r_, p_, q_, n_, partials_, S_);
+            }
+            {
+                TraceScope t("k_cg_direction", s_);
+                k_cg_direction<WT><<<blocks_, kVecThreads, 0, s_>>>(p_, r_, n_, S_);
+            }
+            count_launches(3);
+        }
+        return ARGCSR_OK;
+    }
+
+    argcsr_status enqueue_readback() {
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hS_, S_, sizeof(CgState), cudaMemcpyDeviceToHost, s_);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_, s_);
+        return e == cudaSuccess ? ARGCSR_OK : fail(record_cuda(e, "cg job step"));
+    }
+
+    Operator op_;
+    long long n_;
+    const double *b_;
+    double *x_;
+    argcsr_cg_params P_;
+    cudaStream_t s_;
+    int blocks_;
+    WT *r_ = nullptr, *p_ = nullptr, *q_ = nullptr, *d_ = nullptr;
+    double *r64_ = nullptr, *partials_ = nullptr;
+    CgState *S_ = nullptr, *hS_ = nullptr;
+    cudaEvent_t ev_ = nullptr;
+    cudaGraphExec_t inner_exec_ = nullptr;
+    bool graph_ok_ = false;
+    Phase phase_ = OuterCheck;
+    argcsr_status status_ = ARGCSR_OK;
+    double inner_tol_ = 0, target_ = 0, rel_ = 0;
+    int check_ = 16, outer_ = 0, inner_total_ = 0;
+    bool converged_ = false;
 };
 
-#define SOLVER_CHECK(expr)                              \
-    do {                                                \
-        argcsr_status st_ = (expr);                     \
-        if (st_ != ARGCSR_OK) return st_;               \
-    } while (0)
-
-template <typename WT>
-argcsr_status cg_solve(const Operator &op, long long n, const double *b, double *x,
-                       const argcsr_cg_params &P, cudaStream_t s, argcsr_cg_result *res) {
-    Workspace<WT> w;
-    w.s = s;
-    const size_t vb = (size_t)n * sizeof(WT);
-    SOLVER_CHECK(pool_alloc((void **)&w.r, vb, s));
-    SOLVER_CHECK(pool_alloc((void **)&w.p, vb, s));
-    SOLVER_CHECK(pool_alloc((void **)&w.q, vb, s));
-    SOLVER_CHECK(pool_alloc((void **)&w.d, vb, s));
-    SOLVER_CHECK(pool_alloc((void **)&w.r64, (size_t)n * 8, s));
-    SOLVER_CHECK(pool_alloc((void **)&w.partials, (size_t)kVecBlocks * 8, s));
-    SOLVER_CHECK(pool_alloc((void **)&w.S, sizeof(CgState), s));
-    cudaError_t e = cudaMemsetAsync(w.S, 0, sizeof(CgState), s);
-    if (e != cudaSuccess) return record_cuda(e, "cudaMemsetAsync");
-
-    auto read_state = [&]() -> argcsr_status {
-        cudaError_t er = cudaMemcpyAsync(w.hS, w.S, sizeof(CgState), cudaMemcpyDeviceToHost, s);
-        if (er == cudaSuccess) er = cudaStreamSynchronize(s);
-        return er == cudaSuccess ? ARGCSR_OK : record_cuda(er, "cg: read state");
-    };
-    const dim3 grid(kVecBlocks), block(kVecThreads);
-    {
-        TraceScope t("k_norm2_f64", s);
-        k_norm2_f64<<<grid, block, 0, s>>>(b, n, w.partials, w.S, 1);
+// Run a job to the end on its stream.
+argcsr_status run_to_end(CgJob &job, argcsr_cg_result *res) {
+    argcsr_status st = job.start();
+    while (st == ARGCSR_OK && !job.finished()) {
+        st = job.wait_step();
+        if (st == ARGCSR_OK) st = job.advance();
     }
-    count_launches(1);
-    int inner_total = 0, outer = 0;
-    double rel = 0.0;
-    bool converged = false;
-    const double inner_tol = P.inner_tol > 0 ? P.inner_tol : (sizeof(WT) == 4 ? 1e-5 : P.tol);
-    const int check = P.check_every > 0 ? P.check_every : 16;
-    for (;;) {
-        SOLVER_CHECK(op.residual(b, x, w.r64, s));
-        {
-            TraceScope t("k_norm2_f64", s);
-            k_norm2_f64<<<grid, block, 0, s>>>(w.r64, n, w.partials, w.S, 0);
-        }
-        count_launches(1);
-        ARGCSR_CHECK_LAUNCH("cg residual norm");
-        SOLVER_CHECK(read_state());
-        const double bn = sqrt(w.hS->bnorm2);
-        rel = bn > 0 ? sqrt(w.hS->norm2) / bn : sqrt(w.hS->norm2);
-        if (rel <= P.tol) { converged = true; break; }
-        if (outer >= P.max_outer || inner_total >= P.max_iters) break;
-        ++outer;
-        // inner CG on A d = r / ||r||: reduce its residual by what is still
-        // missing (with a 4x margin), but not below what the working
-        // precision can reach (inner_tol)
-        {
-            TraceScope t("k_ir_start", s);
-            k_ir_start<WT><<<grid, block, 0, s>>>(w.r64, w.r, w.p, w.d, n, w.partials, w.S);
-        }
-        count_launches(1);
-        const double need = rel > 0 ? 0.25 * P.tol / rel : inner_tol;
-        const double step_tol = need > inner_tol ? need : inner_tol;
-        const double target = step_tol * step_tol;
-        for (;;) {
-            for (int k = 0; k < check; ++k) {
-                SOLVER_CHECK(op.apply(w.p, w.q, s));
-                {
-                    TraceScope t("k_cg_alpha", s);
-                    k_cg_alpha<WT><<<grid, block, 0, s>>>(w.p, w.q, n, w.partials, w.S);
-                }
-                {
-                    TraceScope t("k_cg_update", s);
-                    k_cg_update<WT><<<grid, block, 0, s>>>(w.d, w.r, w.p, w.q, n, w.partials, w.S);
-                }
-                {
-                    TraceScope t("k_cg_direction", s);
-                    k_cg_direction<WT><<<grid, block, 0, s>>>(w.p, w.r, n, w.S);
-                }
-                count_launches(3);
-            }
-            ARGCSR_CHECK_LAUNCH("cg inner iteration");
-            inner_total += check;
-            SOLVER_CHECK(read_state());
-            const CgState &h = *w.hS;
-            if (!(h.rho > target * h.rho0) || inner_total >= P.max_iters) break;
-        }
-        {
-            TraceScope t("k_ir_correct", s);
-            k_ir_correct<WT><<<grid, block, 0, s>>>(x, w.d, n, w.S);
-        }
-        count_launches(1);
-    }
-    if (res) {
-        res->outer_iters = outer;
-        res->inner_iters = inner_total;
-        res->converged = converged ? 1 : 0;
-        res->rel_residual = rel;
-    }
-    return ARGCSR_OK;
+    if (st == ARGCSR_OK) st = job.status();
+    if (st == ARGCSR_OK && res) job.result(res);
+    return st;
 }
 
 argcsr_status check_params(const argcsr_cg_params *P) {
@@ -315,6 +462,20 @@ argcsr_status check_params(const argcsr_cg_params *P) {
 }
 
 }  // namespace
+
+CgJob *make_cg_job(const argcsr_matrix *A, const argcsr_matrix *Ares, const double *b, double *x,
+                   const argcsr_cg_params &P, cudaStream_t s) {
+    Operator op;
+    op.A = A;
+    op.Ares = Ares ? Ares : A;
+    if (A->dtype == ARGCSR_F64) return new (std::nothrow) CgJobT<double>(op, A->n_rows, b, x, P, s);
+    return new (std::nothrow) CgJobT<float>(op, A->n_rows, b, x, P, s);
+}
+
+size_t cg_job_bytes(const argcsr_matrix *A) {
+    return A->dtype == ARGCSR_F64 ? CgJobT<double>::bytes_for(A->n_rows) : CgJobT<float>::bytes_for(A->n_rows);
+}
+
 }  // namespace argcsr
 
 using namespace argcsr;
@@ -341,12 +502,12 @@ ARGCSR_API argcsr_status argcsr_cg_solve(argcsr_t A, argcsr_t A_residual, const 
         return ARGCSR_OK;
     }
     if (!d_b || !d_x) return ARGCSR_EINVAL;
-    Operator op;
-    op.A = A;
-    op.Ares = R;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if (A->dtype == ARGCSR_F64) return cg_solve<double>(op, A->n_rows, d_b, d_x, *params, s, result);
-    return cg_solve<float>(op, A->n_rows, d_b, d_x, *params, s, result);
+    CgJob *job = make_cg_job(A, R, d_b, d_x, *params, s);
+    if (!job) return ARGCSR_ENOMEM;
+    st = run_to_end(*job, result);
+    delete job;
+    return st;
 }
 
 ARGCSR_API argcsr_status argcsr_baseline_csr_cg(int32_t n, int64_t nnz, const int32_t *d_rowPointers,
@@ -369,7 +530,8 @@ ARGCSR_API argcsr_status argcsr_baseline_csr_cg(int32_t n, int64_t nnz, const in
     op.rp = d_rowPointers;
     op.cols = d_columns;
     op.vals = d_values;
-    return cg_solve<double>(op, n, d_b, d_x, *params, reinterpret_cast<cudaStream_t>(stream), result);
+    CgJobT<double> job(op, n, d_b, d_x, *params, reinterpret_cast<cudaStream_t>(stream));
+    return run_to_end(job, result);
 }
 
 }  // extern "C"

@@ -463,6 +463,12 @@ argcsr_status launch_batch(const argcsr_batch *B, int k, const void *X, void *Y,
 }
 
 }  // namespace
+
+argcsr_status launch_spmm_public(const argcsr_matrix *A, int k, const void *X, long long ldx, void *Y,
+                                 long long ldy, cudaStream_t s) {
+    return launch_spmm(A, k, X, ldx, Y, ldy, s);
+}
+
 }  // namespace argcsr
 
 using namespace argcsr;

@@ -37,6 +37,11 @@ int trace_start(const char *name, cudaStream_t s) {
     return (int)g_records.size() - 1;
 }
 
+bool trace_active() {
+    std::lock_guard<std::mutex> lock(g_mu);
+    return g_on;
+}
+
 void trace_stop(int token, cudaStream_t s) {
     if (token < 0) return;
     std::lock_guard<std::mutex> lock(g_mu);

@@ -294,6 +294,100 @@ def diag_dominant_batch(count: int = 4096, n_min: int = 100, n_max: int = 20000,
         return pool.map(_diag_dominant_member, jobs, chunksize=16)
 
 
+def _merged_csr(n_rows, n_cols, rows, cols, vals):
+    """CSR from (row, col, value) triples, repeated positions summed,
+    columns sorted within each row."""
+    import scipy.sparse as sp
+    S = sp.coo_matrix((vals, (rows, cols)), shape=(n_rows, n_cols)).tocsr()
+    S.sum_duplicates()
+    S.sort_indices()
+    return S
+
+
+def spd_lognormal(n: int, rng, mu: float = 1.8, sigma: float = 1.0, max_len: int = 512,
+                  dtype=np.float64) -> Csr:
+    """Symmetrised diagonally dominant build (SPD) with uneven rows: row i
+    draws clip(rint(lognormal(mu, sigma)), 1, max_len) - 1 partners j != i
+    uniformly, each draw adding the same N(0, 1) value to a_ij and a_ji
+    (repeated pairs add up, summed once for both); the diagonal is
+    1 + sum_j |a_ij|."""
+    if n < 2:
+        raise ValueError("n must be at least 2")
+    cnt = np.clip(np.rint(rng.lognormal(mu, sigma, n)), 1, min(max_len, n)).astype(np.int64) - 1
+    i = np.repeat(np.arange(n, dtype=np.int64), cnt)
+    j = rng.integers(0, n - 1, i.size, dtype=np.int64)
+    j += j >= i
+    v = rng.standard_normal(i.size)
+    U = _merged_csr(n, n, np.minimum(i, j), np.maximum(i, j), v)     # upper triangle, repeats summed
+    d = np.arange(n, dtype=np.int64)
+    ur = np.repeat(d, np.diff(U.indptr))
+    uc = U.indices.astype(np.int64)
+    diag = 1.0 + np.bincount(ur, weights=np.abs(U.data), minlength=n) \
+        + np.bincount(uc, weights=np.abs(U.data), minlength=n)
+    S = _merged_csr(n, n, np.concatenate([ur, uc, d]), np.concatenate([uc, ur, d]),
+                    np.concatenate([U.data, U.data, diag]))
+    return Csr(n, n, S.indptr.astype(np.int32), S.indices.astype(np.int32), S.data.astype(dtype),
+               f"spd_lognormal_{n}")
+
+
+def zipf_merged(n: int, rng, s: float = 1.5, max_len: int = 50000, dtype=np.float64) -> Csr:
+    """Power-law rows, fast to build: row i draws min(Zipf(s), max_len, n)
+    entries with columns uniform over [0, n) and values N(0, 1); repeated
+    columns in a row are merged (values summed), so long rows come out a
+    little shorter than drawn."""
+    lengths = np.minimum(rng.zipf(s, n), min(max_len, n)).astype(np.int64)
+    rows = np.repeat(np.arange(n, dtype=np.int64), lengths)
+    cols = rng.integers(0, n, rows.size, dtype=np.int64)
+    S = _merged_csr(n, n, rows, cols, rng.standard_normal(rows.size))
+    return Csr(n, n, S.indptr.astype(np.int32), S.indices.astype(np.int32), S.data.astype(dtype),
+               f"zipf_merged_{n}_s{s}")
+
+
+SERVING_KINDS = ("laplace2d", "laplace3d", "spd_lognormal", "zipf")
+
+
+def _serving_member(args):
+    kind, n, seed, m = args
+    rng = np.random.default_rng([seed, m])
+    if kind == "laplace2d":
+        side = max(2, int(round(np.sqrt(n))))
+        return laplacian_2d(side)
+    if kind == "laplace3d":
+        side = max(2, int(round(n ** (1.0 / 3.0))))
+        return laplacian_3d(side)
+    if kind == "spd_lognormal":
+        return spd_lognormal(n, rng)
+    return zipf_merged(n, rng)
+
+
+def serving_pool(count: int = 64, seed: int = 0, n_min: float = 1e4, n_max: float = 2e6,
+                 zipf_n_max: float = 5e4, workers: int = 1) -> list:
+    """A pool of ``count`` matrices for request serving.  Member m is of kind
+    SERVING_KINDS[m % 4] (2D and 3D Laplacians, ``spd_lognormal``,
+    ``zipf_merged`` with s 1.5 and rows of at most 50 000 entries) with n
+    log-uniform in [n_min, n_max]
+    (Zipf members: at most zipf_n_max rows; stencils: the nearest square or
+    cube), drawn from a generator seeded (seed, m); storage FP32 for even
+    m // 4, BF16 for odd.  Zipf members are not symmetric (SpMV only).
+    Returns dicts with keys A (FP64 values), kind, spd, storage."""
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(np.log(n_min), np.log(n_max), count))
+    jobs = []
+    for m in range(count):
+        kind = SERVING_KINDS[m % 4]
+        n = int(min(sizes[m], zipf_n_max) if kind == "zipf" else sizes[m])
+        jobs.append((kind, n, seed, m))
+    if workers <= 1:
+        mats = [_serving_member(j) for j in jobs]
+    else:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as pool:
+            mats = pool.map(_serving_member, jobs, chunksize=1)
+    return [{"A": A, "kind": j[0], "spd": j[0] != "zipf",
+             "storage": "f32" if (m // 4) % 2 == 0 else "bf16"}
+            for m, (A, j) in enumerate(zip(mats, jobs))]
+
+
 def fig3_example(dtype=np.float64) -> Csr:
     """The worked example of Section 3 (Fig. 3 text): an 8x8 matrix whose
     rows 0-6 hold one nonzero each and whose last row is full.  The figure

@@ -189,21 +189,29 @@ def measured_hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_digest():
+# the source files that hold each profiled kernel's code
+KERNEL_SOURCES = {"k_fill": ("convert.cu", "device.cuh"),
+                  "k_groups": ("convert.cu", "device.cuh"),
+                  "k_tile_prepare": ("convert.cu", "device.cuh"),
+                  "k_spmv_g32": ("spmv.cu", "device.cuh")}
+
+
+def kernel_source_digest(kernel):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1203_5737_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(f.read())
+    for name in KERNEL_SOURCES.get(kernel, ()):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel):
     """DRAM bytes per launch from profiles/traffic.txt, if they were taken on
-    the current kernel sources (else None)."""
+    the current sources of that kernel (else None)."""
+    if kernel not in KERNEL_SOURCES:
+        return None
     path = os.path.join(ROOT, "profiles", "traffic.txt")
-    digest = kernel_source_digest()
+    digest = kernel_source_digest(kernel)
     try:
         with open(path) as f:
             for line in f:
@@ -364,6 +372,29 @@ def run_ours(args):
     spmv["combined"] = {"gbs": round(spmv_bytes_all / (spmv_ms_all * 1e-3) / 1e9, 1),
                         "frac": round(spmv_bytes_all / (spmv_ms_all * 1e-3) / 1e9 / peak, 4)}
 
+    # what the adaptive step gains: the same SpMV on the layout without it
+    # (every row one thread, same groups) and on Row-grouped CSR / Sliced
+    # ELLPACK (groups of exactly 32 rows, one thread per row)
+    ablation = {}
+    for m in mats:
+        res = {}
+        for key, D, p1 in (("adaptive", m.D, 0), ("one_thread_per_row", m.D, 1),
+                           ("rgcsr_sell32", 1 << 20, 1)):
+            h = api.argcsr_create_from_csr(m.n, m.n_cols, m.nnz, m.rp.data_ptr(), m.cols.data_ptr(),
+                                           m.vals.data_ptr(), api.ARGCSR_F64, GROUP_SIZE, D, 1, s,
+                                           one_thread_per_row=p1)
+            info = api.argcsr_info(h)
+            nbytes = spmv_bytes(m.n, m.n_cols, m.nnz, info.n_groups)
+            r = _time_gbs(torch, stream, lambda: api.argcsr_spmv(h, m.x.data_ptr(), m.y.data_ptr(), s),
+                          nbytes, max(20, args.steps * 5))
+            r.update({"D": D, "groups": info.n_groups, "slots_per_nnz": round(info.n_slots / m.nnz, 4),
+                      "frac": round(r["gbs"] / peak, 4)})
+            res[key] = r
+            api.argcsr_destroy(h, s)
+        for key in ("one_thread_per_row", "rgcsr_sell32"):
+            res[f"speedup_vs_{key}"] = round(res[key]["us"] / res["adaptive"]["us"], 3)
+        ablation[m.name] = res
+
     # end to end: pinned host CSR + x in, y out, through the public API
     h2d = sum(4 * (m.n + 1) + m.nnz * (4 + SV) + m.n_cols * SX for m in mats)
     d2h = sum(m.n * SX for m in mats)
@@ -424,6 +455,7 @@ def run_ours(args):
             "clocks": clocks,
             "spmv": spmv,
             "baselines": baselines,
+            "ablation": ablation,
             "kernels": kernels,
         }
         print(json.dumps(line), flush=True)
@@ -999,7 +1031,7 @@ def main(argv=None):
                         "CG requests on a 64-matrix pool through the serving engine")
     p.add_argument("--batch-count", type=int, default=4096)
     p.add_argument("--requests", type=int, default=600, help="serving: requests per saturation run")
-    p.add_argument("--serve-streams", type=int, default=16, help="serving: stream slots")
+    p.add_argument("--serve-streams", type=int, default=8, help="serving: stream slots")
     args = p.parse_args(argv)
     if args.ncu_case:
         run_ncu_case(args.ncu_case)

@@ -68,11 +68,20 @@ typedef struct argcsr_graph *argcsr_graph_t;
  *                       of chunk c at offset + j*G + c).  V > 1 rounds the
  *                       chunk size up to a multiple of V and stores element j
  *                       of chunk c at offset + (j/V)*G*V + c*V + j%V, so a
- *                       thread reads V consecutive elements at once. */
+ *                       thread reads V consecutive elements at once.
+ *   one_thread_per_row  0: the paper's adaptive step (spare threads of a
+ *                       group go to its longest rows, Section 3 step 2).
+ *                       1: leave it out -- every row keeps one thread and C
+ *                       is the group's longest row, the state the greedy
+ *                       starts from.  With D * G above the nonzeros of any
+ *                       G consecutive rows every group holds G rows and the
+ *                       layout is Sliced ELLPACK / Row-grouped CSR (Section
+ *                       2).  For measuring what the adaptive step gains. */
 typedef struct {
     int32_t group_size;
     int32_t desired_chunk_size;
     int32_t vec_width;
+    int32_t one_thread_per_row;
 } argcsr_params;
 
 /* Sizes of a converted matrix. */
@@ -90,6 +99,8 @@ typedef struct {
                                   + 4) + n_cols*x + n_rows*y + 4*n_rows
                                   + 16*n_groups (padding not counted)        */
     int64_t device_bytes;      /* device memory the handle holds             */
+    int32_t one_thread_per_row;
+    int32_t reserved;
 } argcsr_info_t;
 
 /* ---------------------------------------------------------------------------
@@ -215,7 +226,8 @@ ARGCSR_API argcsr_status argcsr_batch_destroy(argcsr_batch_t batch, argcsr_strea
  * on the matrix (Section 5: regular matrices want large values, irregular
  * ones small) and uses 128 threads per block; this call converts the CSR
  * input with every candidate (G in the bits of group_size_mask: 1 = 32,
- * 2 = 64, 4 = 128; D in {1, 2, 3, 4, 6, 8, 12, 16, 32}; V = 1), times
+ * 2 = 64, 4 = 128; bit 8 adds the one-thread-per-row layouts of each G;
+ * D in {1, 2, 3, 4, 6, 8, 12, 16, 32}; V = 1), times
  * `reps` products with k right-hand sides, and returns the fastest in *best
  * (its time per product in *best_us).  Candidates whose layout has the same
  * size as one already timed are skipped.  Synchronous on `stream`.

@@ -70,9 +70,11 @@ def _bind(lib):
     lib.oracle_greedy_chunk_size.argtypes = [i32, p, i32]
     lib.oracle_greedy_chunk_size.restype = i64
     lib.oracle_argcsr_structure.argtypes = [i32, p, i32, i32, i32, p, p, p, p]
+    lib.oracle_argcsr_structure_mode.argtypes = [i32, p, i32, i32, i32, i32, p, p, p, p]
     lib.oracle_argcsr_fill.argtypes = [i32, i32, p, p, p, i32, i32, i32, p, i64, p, p, p, i64]
     lib.oracle_argcsr_spmv_f64.argtypes = [i64, p, p, p, p, i64, i32, i32, i32, p, p]
     for f in ("oracle_csr_spmv_f64", "oracle_csr_abs_spmv_f64", "oracle_argcsr_structure",
+              "oracle_argcsr_structure_mode",
               "oracle_argcsr_fill", "oracle_argcsr_spmv_f64"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
@@ -134,22 +136,27 @@ def greedy_chunk_size(lengths, G: int) -> int:
     return int(_load().oracle_greedy_chunk_size(ln.size, _ptr(ln), G))
 
 
-def structure(rowPointers, G: int, desiredChunkSize: int, V: int = 1):
+def structure(rowPointers, G: int, desiredChunkSize: int, V: int = 1, one_thread_per_row=False):
     """Conversion steps 1-3 (Section 3).  Returns (status, groupInfo[n_groups, 4],
-    threadsMapping[n_rows], n_groups, n_slots)."""
+    threadsMapping[n_rows], n_groups, n_slots).  one_thread_per_row leaves out
+    the adaptive step (every row keeps one thread)."""
     rp = np.ascontiguousarray(rowPointers, dtype=np.int32)
     n = rp.size - 1
     lib = _load()
     ng = ctypes.c_int64()
     ns = ctypes.c_int64()
-    st = lib.oracle_argcsr_structure(n, _ptr(rp), G, desiredChunkSize, V, None, None,
-                                     ctypes.byref(ng), ctypes.byref(ns))
+    if one_thread_per_row:
+        call = lambda gi, tm: lib.oracle_argcsr_structure_mode(  # noqa: E731
+            n, _ptr(rp), G, desiredChunkSize, V, 1, gi, tm, ctypes.byref(ng), ctypes.byref(ns))
+    else:
+        call = lambda gi, tm: lib.oracle_argcsr_structure(  # noqa: E731
+            n, _ptr(rp), G, desiredChunkSize, V, gi, tm, ctypes.byref(ng), ctypes.byref(ns))
+    st = call(None, None)
     if st not in (OK, EOVERFLOW):
         return st, None, None, 0, 0
     gi = np.empty((ng.value, 4), dtype=np.int32)
     tm = np.empty(n, dtype=np.int32)
-    st = lib.oracle_argcsr_structure(n, _ptr(rp), G, desiredChunkSize, V, _ptr(gi), _ptr(tm),
-                                     ctypes.byref(ng), ctypes.byref(ns))
+    st = call(_ptr(gi), _ptr(tm))
     return st, gi, tm, ng.value, ns.value
 
 
@@ -172,9 +179,9 @@ class ArgCsr:
         return self.columns.size
 
 
-def convert(A, G: int, desiredChunkSize: int, V: int = 1) -> ArgCsr:
+def convert(A, G: int, desiredChunkSize: int, V: int = 1, one_thread_per_row=False) -> ArgCsr:
     """CSR -> ARG-CSR (Section 3), all steps.  Values keep their dtype."""
-    st, gi, tm, ng, ns = structure(A.rowPointers, G, desiredChunkSize, V)
+    st, gi, tm, ng, ns = structure(A.rowPointers, G, desiredChunkSize, V, one_thread_per_row)
     _check(st, "structure")
     vals = np.ascontiguousarray(A.values)
     out_c = np.empty(ns, dtype=np.int32)

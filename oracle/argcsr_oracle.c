@@ -22,6 +22,11 @@
  *                            example of Fig. 3 (greedy thread assignment).
  *   oracle_argcsr_structure  Section 3, steps 1-3 plus the group layout of
  *                            Listing 1 (firstRow, size, offset, chunkSize).
+ *   oracle_argcsr_structure_mode  the same, optionally without the adaptive
+ *                            step: every row keeps the one thread the greedy
+ *                            starts with (Section 3 step 2's starting state;
+ *                            Sliced ELLPACK / Row-grouped CSR of Section 2
+ *                            when every group holds G rows).
  *   oracle_argcsr_fill       Section 3, last step (chunk-wise copy) with the
  *                            interleaved layout of Section 3 / Fig. 3 and the
  *                            column -1 padding of Section 4.
@@ -190,15 +195,16 @@ int64_t oracle_greedy_chunk_size(int32_t size, const int64_t *len, int32_t G)
  * *n_slots_out always receive the totals, also when the status is
  * ORACLE_EOVERFLOW (more than 2^31 - 1 slots, A10).
  * ---------------------------------------------------------------------- */
-int oracle_argcsr_structure(int32_t n_rows, const int32_t *rowPointers, int32_t G,
-                            int32_t desiredChunkSize, int32_t V,
-                            int32_t *groupInfo, int32_t *threadsMapping,
-                            int64_t *n_groups_out, int64_t *n_slots_out)
+int oracle_argcsr_structure_mode(int32_t n_rows, const int32_t *rowPointers, int32_t G,
+                                 int32_t desiredChunkSize, int32_t V, int32_t one_thread_per_row,
+                                 int32_t *groupInfo, int32_t *threadsMapping,
+                                 int64_t *n_groups_out, int64_t *n_slots_out)
 {
     *n_groups_out = 0;
     *n_slots_out = 0;
     if (n_rows < 0 || G < 1 || G > ORACLE_MAX_G || desiredChunkSize < 1) return ORACLE_EINVAL;
     if (V != 1 && V != 2 && V != 4) return ORACLE_EINVAL;
+    if (one_thread_per_row != 0 && one_thread_per_row != 1) return ORACLE_EINVAL;
     int st = check_csr(n_rows, 0, rowPointers, NULL);
     if (st) return st;
 
@@ -215,7 +221,10 @@ int oracle_argcsr_structure(int32_t n_rows, const int32_t *rowPointers, int32_t 
             int32_t r = firstRow[g] + i;
             len[i] = rowPointers[r + 1] - rowPointers[r];
         }
-        int64_t chunk = oracle_greedy_chunk_size(size[g], len, G);
+        /* the greedy with G threads; without the adaptive step it has no
+         * spare thread to place (a budget of one thread per row), so C is
+         * the longest row: the starting state of step 2 */
+        int64_t chunk = oracle_greedy_chunk_size(size[g], len, one_thread_per_row ? size[g] : G);
         if (chunk > 0) chunk = ceil_div(chunk, V) * V;          /* A13 */
         int64_t prefix = 0;
         for (int32_t i = 0; i < size[g]; i++) {
@@ -237,6 +246,15 @@ int oracle_argcsr_structure(int32_t n_rows, const int32_t *rowPointers, int32_t 
     *n_groups_out = n_groups;
     *n_slots_out = offset;
     return offset > INT32_MAX ? ORACLE_EOVERFLOW : ORACLE_OK;
+}
+
+int oracle_argcsr_structure(int32_t n_rows, const int32_t *rowPointers, int32_t G,
+                            int32_t desiredChunkSize, int32_t V,
+                            int32_t *groupInfo, int32_t *threadsMapping,
+                            int64_t *n_groups_out, int64_t *n_slots_out)
+{
+    return oracle_argcsr_structure_mode(n_rows, rowPointers, G, desiredChunkSize, V, 0, groupInfo,
+                                        threadsMapping, n_groups_out, n_slots_out);
 }
 
 /* -------------------------------------------------------------------------

@@ -23,7 +23,7 @@ ARGCSR_F64, ARGCSR_F32, ARGCSR_BF16 = 0, 1, 2
 
 class argcsr_params(ctypes.Structure):
     _fields_ = [("group_size", ctypes.c_int32), ("desired_chunk_size", ctypes.c_int32),
-                ("vec_width", ctypes.c_int32)]
+                ("vec_width", ctypes.c_int32), ("one_thread_per_row", ctypes.c_int32)]
 
 
 class argcsr_info_t(ctypes.Structure):
@@ -31,10 +31,11 @@ class argcsr_info_t(ctypes.Structure):
                 ("n_groups", ctypes.c_int64), ("n_slots", ctypes.c_int64),
                 ("group_size", ctypes.c_int32), ("desired_chunk_size", ctypes.c_int32),
                 ("vec_width", ctypes.c_int32), ("dtype", ctypes.c_int32),
-                ("spmv_bytes", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+                ("spmv_bytes", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("one_thread_per_row", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
 class argcsr_cg_params(ctypes.Structure):
@@ -215,9 +216,10 @@ def trace_summary() -> dict:
 
 
 def argcsr_create_from_csr(n_rows, n_cols, nnz, d_rowPointers, d_columns, d_values, dtype,
-                           group_size, desired_chunk_size, vec_width=1, stream=0) -> int:
+                           group_size, desired_chunk_size, vec_width=1, stream=0,
+                           one_thread_per_row=0) -> int:
     """Returns the handle (an int); raises ArgcsrError on a non-OK status."""
-    p = argcsr_params(group_size, desired_chunk_size, vec_width)
+    p = argcsr_params(group_size, desired_chunk_size, vec_width, int(one_thread_per_row))
     out = ctypes.c_void_p()
     st = load_library().argcsr_create_from_csr(n_rows, n_cols, nnz, d_rowPointers, d_columns,
                                                d_values, dtype, ctypes.byref(p), stream,
@@ -258,7 +260,7 @@ def argcsr_convert_noalloc(n_rows, n_cols, nnz, d_rowPointers, d_columns, d_valu
     """The conversion into caller-owned buffers, allocating nothing.  Returns
     (status, n_groups, n_slots) without raising, so a caller can size its
     buffers from a first call with zero capacities."""
-    p = argcsr_params(group_size, desired_chunk_size, vec_width)
+    p = argcsr_params(group_size, desired_chunk_size, vec_width, 0)
     ng, ns = ctypes.c_int64(), ctypes.c_int64()
     st = load_library().argcsr_convert_noalloc(
         n_rows, n_cols, nnz, d_rowPointers, d_columns, d_values, dtype, ctypes.byref(p),
@@ -319,13 +321,14 @@ def argcsr_batch_destroy(B, stream=0) -> None:
 
 def argcsr_autotune(n_rows, n_cols, nnz, d_rowPointers, d_columns, d_values, dtype, k=1,
                     group_size_mask=7, reps=10, stream=0):
-    """Returns ((group_size, desired_chunk_size, vec_width), microseconds)."""
+    """Returns ((group_size, desired_chunk_size, vec_width, one_thread_per_row),
+    microseconds).  Bit 8 of group_size_mask adds one-thread-per-row layouts."""
     best = argcsr_params()
     us = ctypes.c_float()
     _check(load_library().argcsr_autotune(n_rows, n_cols, nnz, d_rowPointers, d_columns, d_values,
                                           dtype, k, group_size_mask, reps, stream,
                                           ctypes.byref(best), ctypes.byref(us)), "argcsr_autotune")
-    return (best.group_size, best.desired_chunk_size, best.vec_width), us.value
+    return (best.group_size, best.desired_chunk_size, best.vec_width, best.one_thread_per_row), us.value
 
 
 def argcsr_autotune_batch(n_rows, n_cols, nnz, rp_ptrs, col_ptrs, val_ptrs, dtype, k=1, reps=5,
@@ -495,7 +498,7 @@ class ArgCsrMatrix:
 
     @classmethod
     def from_csr(cls, rowPointers, columns, values, n_cols, group_size=32, desired_chunk_size=4,
-                 vec_width=1, stream=None):
+                 vec_width=1, stream=None, one_thread_per_row=False):
         torch = _torch()
         _check_cuda("rowPointers", rowPointers, torch.int32)
         _check_cuda("columns", columns, torch.int32)
@@ -506,7 +509,8 @@ class ArgCsrMatrix:
             raise ValueError("values and columns differ in length")
         h = argcsr_create_from_csr(n_rows, n_cols, nnz, _ptr(rowPointers), _ptr(columns),
                                    _ptr(values), _dtype_code(values.dtype), group_size,
-                                   desired_chunk_size, vec_width, _stream(stream))
+                                   desired_chunk_size, vec_width, _stream(stream),
+                                   int(one_thread_per_row))
         return cls(h)
 
     @property

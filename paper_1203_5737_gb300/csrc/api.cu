@@ -114,6 +114,8 @@ ARGCSR_API argcsr_status argcsr_info(argcsr_t A, argcsr_info_t *out) {
     out->group_size = A->G;
     out->desired_chunk_size = A->D;
     out->vec_width = A->V;
+    out->one_thread_per_row = A->one_per_row;
+    out->reserved = 0;
     out->dtype = A->dtype;
     const int64_t sv = (int64_t)dtype_size(A->dtype), sx = (int64_t)vec_size(A->dtype);
     out->spmv_bytes = A->nnz * (sv + 4) + (int64_t)A->n_cols * sx + (int64_t)A->n_rows * sx +

@@ -255,7 +255,7 @@ __device__ __forceinline__ unsigned ceil_div_by(unsigned l, unsigned d, unsigned
 // ---------------------------------------------------------------------------
 template <int G>
 __global__ void __launch_bounds__(kTileThreads)
-k_groups(int n, int T, int V, const int *__restrict__ rp, const uint8_t *__restrict__ delta,
+k_groups(int n, int T, int V, int onePerRow, const int *__restrict__ rp, const uint8_t *__restrict__ delta,
          const int *__restrict__ tileEntry, const int *__restrict__ tileGroupBase,
          int4 *__restrict__ gscratch, int *__restrict__ threadsMapping,
          long long *__restrict__ tileSlots, DeviceTotals *tot) {
@@ -325,7 +325,12 @@ k_groups(int n, int T, int V, const int *__restrict__ rp, const uint8_t *__restr
             nnz += L[r];
         }
         long long C = 0;
-        if (maxlen > 0) {
+        if (maxlen > 0 && onePerRow) {
+            // no thread assignment: every row keeps one thread, so C is the
+            // longest row -- the state the greedy starts from (Sliced
+            // ELLPACK / Row-grouped CSR, Section 2)
+            C = ((long long)maxlen + V - 1) / V * V;
+        } else if (maxlen > 0) {
             // C >= nnz / G (all threads busy) and C >= maxlen / (G - size + 1)
             // (the longest row gets at most the spare threads plus its own)
             unsigned lo = (unsigned)max((nnz + G - 1) / G,
@@ -535,7 +540,7 @@ inline size_t prepare_smem(int T, int G) {
 template <int G>
 struct Kernels {
     static argcsr_status run_structure(int n, long long nnz, long long limit, int T, int numTiles,
-                                       int V, const int *rp, uint8_t *delta, uint8_t *fn, int *cnt,
+                                       int V, int onePerRow, const int *rp, uint8_t *delta, uint8_t *fn, int *cnt,
                                        int *tileEntry, int *tileGroupBase, int4 *gscratch, int *tm,
                                        long long *tileSlots, long long *tileSlotBase,
                                        DeviceTotals *tot, cudaStream_t s) {
@@ -551,7 +556,7 @@ struct Kernels {
         {
             TraceScope t("k_groups", s);
             const size_t smem = groups_smem(T, G);
-            k_groups<G><<<numTiles, kTileThreads, smem, s>>>(n, T, V, rp, delta, tileEntry, tileGroupBase,
+            k_groups<G><<<numTiles, kTileThreads, smem, s>>>(n, T, V, onePerRow, rp, delta, tileEntry, tileGroupBase,
                                                      gscratch, tm, tileSlots, tot);
         }
         {
@@ -610,7 +615,9 @@ extern "C" ARGCSR_API argcsr_status argcsr_create_from_csr(
     *out = nullptr;
     if (!params || n_rows < 0 || n_cols < 0 || nnz < 0 || nnz > 0x7fffffffLL) return ARGCSR_EINVAL;
     const int G = params->group_size, D = params->desired_chunk_size, V = params->vec_width;
+    const int P1 = params->one_thread_per_row;
     if ((G != 32 && G != 64 && G != 128) || D < 1 || (V != 1 && V != 2 && V != 4)) return ARGCSR_EINVAL;
+    if (P1 != 0 && P1 != 1) return ARGCSR_EINVAL;
     if (dtype != ARGCSR_F64 && dtype != ARGCSR_F32 && dtype != ARGCSR_BF16) return ARGCSR_EINVAL;
     if (!d_rowPointers || (nnz > 0 && (!d_columns || !d_values))) return ARGCSR_EINVAL;
     if (n_rows == 0 && nnz != 0) return ARGCSR_EINVAL;
@@ -619,7 +626,7 @@ extern "C" ARGCSR_API argcsr_status argcsr_create_from_csr(
     argcsr_matrix *A = new argcsr_matrix();
     cudaGetDevice(&A->device);
     A->n_rows = n_rows; A->n_cols = n_cols; A->nnz = nnz;
-    A->G = G; A->D = D; A->V = V; A->dtype = dtype;
+    A->G = G; A->D = D; A->V = V; A->one_per_row = P1; A->dtype = dtype;
     auto fail = [&](argcsr_status st) { argcsr_destroy(A, stream); return st; };
     if (n_rows == 0) { *out = A; return ARGCSR_OK; }
 
@@ -657,9 +664,9 @@ extern "C" ARGCSR_API argcsr_status argcsr_create_from_csr(
     if (e != cudaSuccess) return fail(record_cuda(e, "cudaMemsetAsync"));
     const long long limit = (long long)D * G;
     switch (G) {
-        case 32: st = set_smem_limits<32>(T); if (!st) st = Kernels<32>::run_structure(n, nnz, limit, T, numTiles, V, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, A->d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
-        case 64: st = set_smem_limits<64>(T); if (!st) st = Kernels<64>::run_structure(n, nnz, limit, T, numTiles, V, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, A->d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
-        default: st = set_smem_limits<128>(T); if (!st) st = Kernels<128>::run_structure(n, nnz, limit, T, numTiles, V, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, A->d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
+        case 32: st = set_smem_limits<32>(T); if (!st) st = Kernels<32>::run_structure(n, nnz, limit, T, numTiles, V, P1, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, A->d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
+        case 64: st = set_smem_limits<64>(T); if (!st) st = Kernels<64>::run_structure(n, nnz, limit, T, numTiles, V, P1, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, A->d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
+        default: st = set_smem_limits<128>(T); if (!st) st = Kernels<128>::run_structure(n, nnz, limit, T, numTiles, V, P1, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, A->d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
     }
     if (st != ARGCSR_OK) return fail(st);
 
@@ -762,7 +769,9 @@ extern "C" ARGCSR_API argcsr_status argcsr_convert_noalloc(
         return ARGCSR_EINVAL;
     }
     const int G = params->group_size, D = params->desired_chunk_size, V = params->vec_width;
+    const int P1 = params->one_thread_per_row;
     if ((G != 32 && G != 64 && G != 128) || D < 1 || (V != 1 && V != 2 && V != 4)) return ARGCSR_EINVAL;
+    if (P1 != 0 && P1 != 1) return ARGCSR_EINVAL;
     if (dtype != ARGCSR_F64 && dtype != ARGCSR_F32 && dtype != ARGCSR_BF16) return ARGCSR_EINVAL;
     if (!d_rowPointers || (nnz > 0 && (!d_columns || !d_values))) return ARGCSR_EINVAL;
     if (n_rows == 0) return nnz == 0 ? ARGCSR_OK : ARGCSR_EINVAL;
@@ -790,9 +799,9 @@ extern "C" ARGCSR_API argcsr_status argcsr_convert_noalloc(
     if (e != cudaSuccess) return record_cuda(e, "cudaMemsetAsync");
     const long long limit = (long long)D * G;
     switch (G) {
-        case 32: st = set_smem_limits<32>(T); if (!st) st = Kernels<32>::run_structure(n, nnz, limit, T, numTiles, V, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
-        case 64: st = set_smem_limits<64>(T); if (!st) st = Kernels<64>::run_structure(n, nnz, limit, T, numTiles, V, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
-        default: st = set_smem_limits<128>(T); if (!st) st = Kernels<128>::run_structure(n, nnz, limit, T, numTiles, V, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
+        case 32: st = set_smem_limits<32>(T); if (!st) st = Kernels<32>::run_structure(n, nnz, limit, T, numTiles, V, P1, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
+        case 64: st = set_smem_limits<64>(T); if (!st) st = Kernels<64>::run_structure(n, nnz, limit, T, numTiles, V, P1, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
+        default: st = set_smem_limits<128>(T); if (!st) st = Kernels<128>::run_structure(n, nnz, limit, T, numTiles, V, P1, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
     }
     if (st != ARGCSR_OK) return st;
     DeviceTotals h;

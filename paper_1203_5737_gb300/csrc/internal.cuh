@@ -33,6 +33,7 @@ struct argcsr_matrix {
     int32_t n_rows, n_cols;
     int64_t nnz;
     int32_t G, D, V;
+    int32_t one_per_row;        // 1: every row one thread (no adaptive step)
     argcsr_dtype dtype;
     int64_t n_groups, n_slots;
     int4 *d_groupInfo;          // {firstRow, size, offset, chunkSize}

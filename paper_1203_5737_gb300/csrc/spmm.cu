@@ -649,11 +649,13 @@ ARGCSR_API argcsr_status argcsr_autotune(int32_t n_rows, int32_t n_cols, int64_t
     struct Seen { int G, V; int64_t groups, slots; };
     std::vector<Seen> seen;
     float bestT = INFINITY;
-    argcsr_params bp{32, 1, 1};
+    argcsr_params bp{32, 1, 1, 0};
+    const int modes = (group_size_mask & 8) ? 2 : 1;
     for (int gi = 0; gi < 3 && st == ARGCSR_OK; ++gi) {
         if (!(group_size_mask & (1 << gi))) continue;
+        for (int mode = 0; mode < modes; ++mode)
         for (int D : Ds) {
-            argcsr_params p{Gs[gi], D, 1};
+            argcsr_params p{Gs[gi], D, 1, mode};
             argcsr_t A = nullptr;
             argcsr_status cs = argcsr_create_from_csr(n_rows, n_cols, nnz, d_rowPointers, d_columns,
                                                       d_values, dtype, &p, stream, &A);
@@ -715,11 +717,11 @@ ARGCSR_API argcsr_status argcsr_autotune_batch(int32_t count, const int32_t *h_n
         st = ARGCSR_ECUDA;
     const int Ds[] = {1, 2, 4, 8, 16, 32};
     float bestT = INFINITY;
-    argcsr_params bp{32, 1, 1};
+    argcsr_params bp{32, 1, 1, 0};
     std::vector<argcsr_t> mats(count, nullptr);
     for (int D : Ds) {
         if (st != ARGCSR_OK) break;
-        argcsr_params p{32, D, 1};
+        argcsr_params p{32, D, 1, 0};
         bool ok = true;
         for (int i = 0; i < count && st == ARGCSR_OK; ++i) {
             argcsr_status cs = argcsr_create_from_csr(h_n_rows[i], h_n_cols[i], h_nnz[i], h_rowPointers[i],

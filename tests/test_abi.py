@@ -69,7 +69,7 @@ def test_argument_checks_without_gpu(lib):
     P = api.argcsr_params(32, 4, 1)
     out = ctypes.c_void_p(123)
     # invalid group size, chunk size, vector width, dtype, sizes: all EINVAL
-    for params in ((16, 4, 1), (32, 0, 1), (32, 4, 3), (256, 1, 1)):
+    for params in ((16, 4, 1), (32, 0, 1), (32, 4, 3), (256, 1, 1), (32, 4, 1, 2), (32, 4, 1, -1)):
         p = api.argcsr_params(*params)
         assert lib.argcsr_create_from_csr(10, 10, 0, 8, None, None, 0, ctypes.byref(p), None,
                                           ctypes.byref(out)) == api.ARGCSR_EINVAL

@@ -77,15 +77,16 @@ def check_y(y, As, x, storage):
     assert np.all(y[lens == 0] == 0)
 
 
-def convert_and_check(A, G, D, V=1, storage="f64", x_seed=0, check_spmv=True):
+def convert_and_check(A, G, D, V=1, storage="f64", x_seed=0, check_spmv=True, one_thread_per_row=False):
     rp, cols, vd, As = to_device(A, storage)
     with ArgCsrMatrix.from_csr(rp, cols, vd, A.n_cols, group_size=G, desired_chunk_size=D,
-                               vec_width=V) as M:
+                               vec_width=V, one_thread_per_row=one_thread_per_row) as M:
         got = M.export()
         info = M.info()
+        assert info["one_thread_per_row"] == int(one_thread_per_row)
         ref_src = synth.Csr(A.n_rows, A.n_cols, A.rowPointers, A.columns,
                             oracle_values(A, storage, vd), A.name)
-        ref = oracle.convert(ref_src, G, D, V)
+        ref = oracle.convert(ref_src, G, D, V, one_thread_per_row=one_thread_per_row)
         assert info["n_groups"] == ref.n_groups
         assert info["n_slots"] == ref.n_slots
         assert np.array_equal(got["groupInfo"], ref.groupInfo)
@@ -117,6 +118,22 @@ def test_random_small(G, D, V):
         A = synth.random_csr(n_rows, n_cols, seed, mean_len=float(rng.uniform(0.5, 30)),
                              p_empty=float(rng.uniform(0, 0.4)), n_huge=int(rng.integers(0, 3)))
         convert_and_check(A, G, D, V)
+
+
+@pytest.mark.parametrize("G", [32, 64, 128])
+@pytest.mark.parametrize("D,V", [(1, 1), (4, 2), (1 << 20, 1), (8, 4)])
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_one_thread_per_row(G, D, V, storage):
+    # the layout without the adaptive step (Sliced ELLPACK / Row-grouped CSR
+    # of the same groups; D = 2^20 makes every group G rows)
+    for seed in range(3):
+        rng = np.random.default_rng(7000 + G + D + V + seed)
+        n_rows = int(rng.integers(1, 5000))
+        n_cols = int(rng.integers(1, 3000))
+        A = synth.random_csr(n_rows, n_cols, seed, mean_len=float(rng.uniform(0.5, 20)),
+                             p_empty=float(rng.uniform(0, 0.4)), n_huge=int(rng.integers(0, 3)),
+                             huge_len=min(n_cols, 600))
+        convert_and_check(A, G, D, V, storage=storage, one_thread_per_row=True)
 
 
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
@@ -315,6 +332,14 @@ def test_overlapping_x_y_rejected():
 def test_full_size_workloads(name, G, D):
     A, _ = synth.workload(name)
     convert_and_check(A, G, D, x_seed=2)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("D", [4, 1 << 20])
+def test_full_size_lognormal_without_adaptive_step(D):
+    # the layouts the bench's ablation times
+    A, _ = synth.workload("lognormal_2m")
+    convert_and_check(A, 32, D, x_seed=2, one_thread_per_row=True)
 
 
 @pytest.mark.slow

@@ -149,10 +149,10 @@ def test_autotune_returns_a_valid_layout():
     v = torch.from_numpy(A.values).to(DEV)
     s = torch.cuda.current_stream().cuda_stream
     for k, mask in ((1, 7), (4, 1)):
-        (G, D, V), us = api.argcsr_autotune(A.n_rows, A.n_cols, A.nnz, rp.data_ptr(), cols.data_ptr(),
+        (G, D, V, P1), us = api.argcsr_autotune(A.n_rows, A.n_cols, A.nnz, rp.data_ptr(), cols.data_ptr(),
                                             v.data_ptr(), api.ARGCSR_F32, k, mask, 3, s)
         assert G in ((32, 64, 128) if mask == 7 else (32,)) and D in (1, 2, 3, 4, 6, 8, 12, 16, 32)
-        assert V == 1 and us > 0
+        assert V == 1 and P1 == 0 and us > 0
         # the chosen layout converts and multiplies like any other
         with ArgCsrMatrix.from_csr(rp, cols, v, A.n_cols, group_size=G, desired_chunk_size=D) as M:
             ref = oracle.convert(A, G, D)

@@ -45,12 +45,16 @@ MUTANTS = {
     "argspmv_begin_index": ("const int32_t begin = i == 0 ? 0 : threadsMapping[r - 1];\n            const int32_t end",
                             "const int32_t begin = i == 0 ? 0 : threadsMapping[r - 1] + 1;\n            const int32_t end"),
     "abs_sum_signed": ("sum += p < 0 ? -p : p;", "sum += p;"),
+    "one_per_row_ignored": ("one_thread_per_row ? size[g] : G", "G"),
+    "one_per_row_spare_thread": ("one_thread_per_row ? size[g] : G", "one_thread_per_row ? size[g] + 1 : G"),
 }
 
 # pins that take no arguments, plus parametrised ones with a few arguments
 PINS = [
     (pins.test_fig3_adaptive_mapping, ()),
     (pins.test_fig3_one_thread_per_row, ()),
+    (pins.test_fig3_without_adaptive_step, ()),
+    (pins.test_one_thread_per_row_is_sliced_ellpack_of_the_groups, (32, 2, 1)),
     (pins.test_fig3_full_conversion_roundtrip, ()),
     (pins.test_greedy_matches_exhaustive_search, ()),
     (pins.test_greedy_matches_min_feasible_chunk, (32,)),

@@ -59,6 +59,26 @@ def test_fig3_one_thread_per_row():
     assert oracle.greedy_chunk_size(lens, gold["threads"]) == gold["adaptive.chunk_size"]
 
 
+def test_fig3_without_adaptive_step():
+    gold, lens, rp = _fig3()
+    # The same 12 threads, but the adaptive step left out: every row keeps one
+    # thread, so the chunk size is the longest row and the 8 used chunks hold
+    # the 49 artificial zeros the example counts; the 4 unused chunks of the
+    # group are padding too (every group owns G chunks).
+    G = gold["threads"]
+    st, gi, tm, ng, ns = oracle.structure(rp, G, 1, one_thread_per_row=True)
+    assert st == oracle.OK and ng == 1
+    chunk = gi[0, 3]
+    assert chunk == gold["one_thread_per_row.chunk_size"]
+    assert list(tm) == list(range(1, 9))
+    assert tm[-1] * chunk - gold["nonzeros"] == gold["one_thread_per_row.artificial_zeros"]
+    assert ns == chunk * G
+    M = oracle.convert(synth.fig3_example(), G, 1, one_thread_per_row=True)
+    used = M.columns.reshape(chunk, G)[:, :8]
+    assert int(np.sum(used < 0)) == gold["one_thread_per_row.artificial_zeros"]
+    assert np.all(M.columns.reshape(chunk, G)[:, 8:] == -1)
+
+
 def test_fig3_full_conversion_roundtrip():
     A = synth.fig3_example()
     M = oracle.convert(A, 12, 1)
@@ -307,6 +327,46 @@ def test_sliced_ellpack_special_case(G):
     assert np.array_equal(M.values, np.concatenate(vals))
     assert np.array_equal(M.threadsMapping, np.tile(np.arange(1, G + 1), n // G))
     del rng
+
+
+@pytest.mark.parametrize("G,D,V", [(32, 2, 1), (64, 1, 1), (32, 3, 2), (128, 4, 4)])
+def test_one_thread_per_row_is_sliced_ellpack_of_the_groups(G, D, V):
+    # Without the adaptive step each group is one Sliced ELLPACK slice
+    # (Section 2) over its own rows: width = its longest row (rounded up to
+    # V), row i of the group is chunk i, and chunks size..G-1 are padding.
+    A = synth.random_csr(900, 700, G + D, mean_len=5, p_empty=0.15, n_huge=3, huge_len=400)
+    M = oracle.convert(A, G, D, V, one_thread_per_row=True)
+    first, size = oracle.group_rows(A.rowPointers, G, D)
+    lens = A.row_lengths()
+    assert np.array_equal(M.groupInfo[:, 0], first) and np.array_equal(M.groupInfo[:, 1], size)
+    offset = 0
+    for g in range(first.size):
+        rows = range(first[g], first[g] + size[g])
+        width = int(max(lens[r] for r in rows))
+        width = -(-width // V) * V
+        assert M.groupInfo[g, 2] == offset and M.groupInfo[g, 3] == width
+        ell_c = -np.ones((width, G), dtype=np.int32)
+        ell_v = np.zeros((width, G))
+        for i, r in enumerate(rows):
+            lo, hi = A.rowPointers[r], A.rowPointers[r + 1]
+            ell_c[:hi - lo, i] = A.columns[lo:hi]
+            ell_v[:hi - lo, i] = A.values[lo:hi]
+        # element j of chunk c at offset + (j / V) G V + c V + j % V
+        j = np.arange(width)[:, None]
+        c = np.arange(G)[None, :]
+        slot = offset + (j // V) * G * V + c * V + j % V
+        assert np.array_equal(M.columns[slot], ell_c)
+        assert np.array_equal(M.values[slot], ell_v)
+        assert list(M.threadsMapping[first[g]:first[g] + size[g]]) == list(range(1, size[g] + 1))
+        offset += width * G
+    assert M.columns.size == offset
+    # the adaptive step never needs more slots, group by group
+    Ma = oracle.convert(A, G, D, V)
+    assert np.all(Ma.groupInfo[:, 3] <= M.groupInfo[:, 3])
+    x = synth.uniform_vector(A.n_cols, 2)
+    ref = A.to_dense() @ x
+    np.testing.assert_allclose(oracle.argcsr_spmv(M, x), ref, rtol=0,
+                               atol=1e-13 * float(np.max(np.abs(A.to_dense()) @ np.abs(x))))
 
 
 # ---------------------------------------------------------------------------

@@ -436,9 +436,9 @@ k_tile_scan(int numTiles, const long long *__restrict__ tileSlots, long long *__
 // ---------------------------------------------------------------------------
 // 6. Group records and the chunk-wise copy (one warp per group).
 // ---------------------------------------------------------------------------
-template <int G, typename VT>
+template <int G, typename VT, int V>
 __global__ void __launch_bounds__(256)
-k_fill(long long nGroups, int V, int n_cols, const long long *__restrict__ tileSlotBase,
+k_fill(long long nGroups, int n_cols, const long long *__restrict__ tileSlotBase,
        const int4 *__restrict__ gscratch, const int *__restrict__ rp, const int *__restrict__ colsIn,
        const VT *__restrict__ valsIn, const int *__restrict__ threadsMapping,
        int4 *__restrict__ groupInfo, int *__restrict__ colsOut, VT *__restrict__ valsOut,
@@ -490,7 +490,13 @@ k_fill(long long nGroups, int V, int n_cols, const long long *__restrict__ tileS
                 fill = (int)min((long long)C, max(0LL, len - kk));
             }
             // a chunk's elements are contiguous in the CSR arrays; lanes of one
-            // row read C apart, which L1 serves from the lines already fetched
+            // row read C apart, which L1 serves from the lines already fetched.
+            // Element j of chunk c goes to off + (j/V)*G*V + c*V + j%V; the
+            // part that depends on j stays below C*G < 2^31.
+            const int *cIn = colsIn + src;
+            const VT *vIn = valsIn + src;
+            int *cOut = colsOut + off + (long long)c * V;
+            VT *vOut = valsOut + off + (long long)c * V;
             for (int j0 = 0; j0 < C; j0 += 4) {
                 int cc[4];
                 VT vv[4];
@@ -500,8 +506,8 @@ k_fill(long long nGroups, int V, int n_cols, const long long *__restrict__ tileS
                     cc[u] = -1;
                     memset(&vv[u], 0, sizeof(VT));
                     if (j < fill) {
-                        cc[u] = colsIn[src + j];
-                        vv[u] = valsIn[src + j];
+                        cc[u] = cIn[j];
+                        vv[u] = vIn[j];
                         bad |= (cc[u] < 0) | (cc[u] >= n_cols);
                     }
                 }
@@ -509,9 +515,9 @@ k_fill(long long nGroups, int V, int n_cols, const long long *__restrict__ tileS
                 for (int u = 0; u < 4; ++u) {
                     const int j = j0 + u;
                     if (j < C) {
-                        const long long slot = off + (long long)(j / V) * G * V + (long long)c * V + (j % V);
-                        colsOut[slot] = cc[u];
-                        valsOut[slot] = vv[u];
+                        const int at = (j / V) * (G * V) + (j % V);
+                        cOut[at] = cc[u];
+                        vOut[at] = vv[u];
                     }
                 }
             }
@@ -576,9 +582,17 @@ struct Kernels {
         if (nGroups == 0) return ARGCSR_OK;
         const long long blocks = min((nGroups + 7) / 8, 152LL * 64);
         TraceScope t("k_fill", s);
-        k_fill<G, VT><<<(unsigned)blocks, 256, 0, s>>>(
-            nGroups, V, n_cols, tileSlotBase, gscratch, rp, cols,
-            static_cast<const VT *>(vals), tm, gi, colsOut, static_cast<VT *>(valsOut), tot);
+        const VT *v = static_cast<const VT *>(vals);
+        VT *vo = static_cast<VT *>(valsOut);
+        if (V == 1)
+            k_fill<G, VT, 1><<<(unsigned)blocks, 256, 0, s>>>(nGroups, n_cols, tileSlotBase, gscratch, rp,
+                                                              cols, v, tm, gi, colsOut, vo, tot);
+        else if (V == 2)
+            k_fill<G, VT, 2><<<(unsigned)blocks, 256, 0, s>>>(nGroups, n_cols, tileSlotBase, gscratch, rp,
+                                                              cols, v, tm, gi, colsOut, vo, tot);
+        else
+            k_fill<G, VT, 4><<<(unsigned)blocks, 256, 0, s>>>(nGroups, n_cols, tileSlotBase, gscratch, rp,
+                                                              cols, v, tm, gi, colsOut, vo, tot);
         count_launches(1);
         ARGCSR_CHECK_LAUNCH("k_fill");
         return ARGCSR_OK;

@@ -372,6 +372,9 @@ ARGCSR_API argcsr_status argcsr_server_query(argcsr_server_t server, int64_t req
 /* Wait for one request (timeout_s <= 0: no limit); ARGCSR_ENOTSUP on timeout. */
 ARGCSR_API argcsr_status argcsr_server_wait(argcsr_server_t server, int64_t request,
                                             double timeout_s, argcsr_request_info *info);
+/* Forget a finished request (its record is kept until then, so that it can
+ * be queried); ARGCSR_EINVAL if it is unknown or not finished. */
+ARGCSR_API argcsr_status argcsr_server_release(argcsr_server_t server, int64_t request);
 /* Wait until every submitted request is done; ARGCSR_ENOTSUP on timeout. */
 ARGCSR_API argcsr_status argcsr_server_drain(argcsr_server_t server, double timeout_s);
 ARGCSR_API argcsr_status argcsr_server_stats(argcsr_server_t server, int64_t *matrix_bytes,

@@ -131,6 +131,7 @@ _SIGNATURES = {
     "argcsr_server_query": (ctypes.c_int, [_P, _I64, ctypes.POINTER(argcsr_request_info)]),
     "argcsr_server_wait": (ctypes.c_int, [_P, _I64, ctypes.c_double, ctypes.POINTER(argcsr_request_info)]),
     "argcsr_server_drain": (ctypes.c_int, [_P, ctypes.c_double]),
+    "argcsr_server_release": (ctypes.c_int, [_P, _I64]),
     "argcsr_server_stats": (ctypes.c_int, [_P] + [ctypes.POINTER(_I64)] * 4),
     "argcsr_server_destroy": (ctypes.c_int, [_P]),
     "argcsr_trace_begin": (ctypes.c_int, []),
@@ -391,6 +392,10 @@ def argcsr_server_wait(S, request, timeout_s=0.0) -> dict:
     _check(load_library().argcsr_server_wait(S, request, timeout_s, ctypes.byref(info)),
            "argcsr_server_wait")
     return info.as_dict()
+
+
+def argcsr_server_release(S, request) -> None:
+    _check(load_library().argcsr_server_release(S, request), "argcsr_server_release")
 
 
 def argcsr_server_drain(S, timeout_s=0.0) -> None:
@@ -667,6 +672,10 @@ class ArgCsrServer:
         info = argcsr_server_wait(self._h, request, timeout_s)
         self._live.pop(request, None)
         return info
+
+    def release(self, request) -> None:
+        argcsr_server_release(self._h, request)
+        self._live.pop(request, None)
 
     def drain(self, timeout_s=0.0) -> None:
         argcsr_server_drain(self._h, timeout_s)

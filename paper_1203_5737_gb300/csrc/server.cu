@@ -444,6 +444,15 @@ ARGCSR_API argcsr_status argcsr_server_wait(argcsr_server_t S, int64_t request, 
     return r->info.state >= 2 ? ARGCSR_OK : ARGCSR_ENOTSUP;
 }
 
+ARGCSR_API argcsr_status argcsr_server_release(argcsr_server_t S, int64_t request) {
+    if (!S) return ARGCSR_EINVAL;
+    std::lock_guard<std::mutex> lock(S->mu);
+    auto it = S->requests.find(request);
+    if (it == S->requests.end() || it->second->info.state < 2) return ARGCSR_EINVAL;
+    S->requests.erase(it);
+    return ARGCSR_OK;
+}
+
 ARGCSR_API argcsr_status argcsr_server_drain(argcsr_server_t S, double timeout_s) {
     if (!S) return ARGCSR_EINVAL;
     std::unique_lock<std::mutex> lock(S->mu);

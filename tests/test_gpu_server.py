@@ -229,6 +229,12 @@ def test_invalid_calls(pool):
         with pytest.raises(api.ArgcsrError) as e:
             S.add_matrix(pool[0]["M"])
         assert e.value.status == api.ARGCSR_EINVAL
+        # a finished request can be forgotten, once
+        S.release(h)
+        with pytest.raises(api.ArgcsrError):
+            S.query(h)
+        with pytest.raises(api.ArgcsrError):
+            S.release(h)
         torch.cuda.synchronize()
 
 

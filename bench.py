@@ -372,6 +372,29 @@ def run_ours(args):
     spmv["combined"] = {"gbs": round(spmv_bytes_all / (spmv_ms_all * 1e-3) / 1e9, 1),
                         "frac": round(spmv_bytes_all / (spmv_ms_all * 1e-3) / 1e9 / peak, 4)}
 
+    # the desiredChunkSize sweep 1..32 (conversion and SpMV time per D)
+    d_sweep = {}
+    if not args.no_sweep:
+        for m in mats:
+            rows = {}
+            for D in range(1, 33):
+                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                h = api.argcsr_create_from_csr(m.n, m.n_cols, m.nnz, m.rp.data_ptr(), m.cols.data_ptr(),
+                                               m.vals.data_ptr(), api.ARGCSR_F64, GROUP_SIZE, D, 1, s)
+                a1.record(stream)
+                torch.cuda.synchronize()
+                info = api.argcsr_info(h)
+                nbytes = spmv_bytes(m.n, m.n_cols, m.nnz, info.n_groups)
+                r = _time_gbs(torch, stream, lambda: api.argcsr_spmv(h, m.x.data_ptr(), m.y.data_ptr(), s),
+                              nbytes, 20)
+                rows[D] = {"convert_us": round(a0.elapsed_time(a1) * 1e3, 1), "spmv_us": r["us"],
+                           "spmv_gbs": r["gbs"], "slots_per_nnz": round(info.n_slots / m.nnz, 4)}
+                api.argcsr_destroy(h, s)
+            best_spmv = min(rows, key=lambda d: rows[d]["spmv_us"])
+            best_step = min(rows, key=lambda d: rows[d]["spmv_us"] + rows[d]["convert_us"])
+            d_sweep[m.name] = {"best_spmv_D": best_spmv, "best_step_D": best_step, "by_D": rows}
+
     # what the adaptive step gains: the same SpMV on the layout without it
     # (every row one thread, same groups) and on Row-grouped CSR / Sliced
     # ELLPACK (groups of exactly 32 rows, one thread per row)
@@ -468,6 +491,7 @@ def run_ours(args):
             "spmv": spmv,
             "baselines": baselines,
             "ablation": ablation,
+            "d_sweep": d_sweep,
             "kernels": kernels,
         }
         print(json.dumps(line), flush=True)
@@ -1032,6 +1056,7 @@ def main(argv=None):
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-sweep", action="store_true", help="skip the desiredChunkSize sweep")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--ncu-case", choices=("small", "bench"),
                    help="run a short untimed launch sequence for ncu, then exit")

@@ -78,10 +78,16 @@ __device__ __forceinline__ void subtile_tables(const uint8_t *d, int lim, int B,
 
 template <int G> constexpr int subtile_rows() { return G > 64 ? G : 64; }
 
+// k_groups keeps per-row values (lengths, threadsMapping) in shared memory
+// with one padding word after every 32: a thread per group walks its rows,
+// and groups that start 32 rows apart would otherwise all hit one bank.
+__host__ __device__ constexpr int pad32(int r) { return r + (r >> 5); }
+__host__ __device__ constexpr size_t padded_rows(int T, int G) { return (size_t)pad32(T + G) + 1; }
+
 // Byte offset of k_groups' threadsMapping staging array in its shared memory
 // (after the parts listed at groups_smem, 4-byte aligned).
 __host__ __device__ constexpr size_t groups_pfx_offset(int T, int G) {
-    return ((size_t)T * 11 + 4 * (size_t)G + 2 * (size_t)(T / (G > 64 ? G : 64)) * G +
+    return ((size_t)T * 7 + 4 * padded_rows(T, G) + 2 * (size_t)(T / (G > 64 ? G : 64)) * G +
             4 * (size_t)(T / (G > 64 ? G : 64)) + 3) & ~size_t(3);
 }
 
@@ -265,12 +271,12 @@ k_groups(int n, int T, int V, int onePerRow, const int *__restrict__ rp, const u
     uint8_t *d = smem;                                              // T bytes
     uint16_t *starts = reinterpret_cast<uint16_t *>(smem + T);      // T entries
     int *chunk = reinterpret_cast<int *>(smem + 3 * (size_t)T);     // T entries
-    int *lens = reinterpret_cast<int *>(smem + 7 * (size_t)T);      // T + G entries
-    uint8_t *fnA = smem + 11 * (size_t)T + 4 * (size_t)G;           // S * G
+    int *lens = reinterpret_cast<int *>(smem + 7 * (size_t)T);      // T + G entries, padded
+    uint8_t *fnA = smem + 7 * (size_t)T + 4 * padded_rows(T, G);    // S * G
     uint8_t *cntA = fnA + (size_t)S * G;                            // S * G
     uint16_t *subEntry = reinterpret_cast<uint16_t *>(cntA + (size_t)S * G);  // S
     uint16_t *subBase = subEntry + S;                                         // S
-    int *pfx = reinterpret_cast<int *>(smem + groups_pfx_offset(T, G));       // T + G
+    int *pfx = reinterpret_cast<int *>(smem + groups_pfx_offset(T, G));       // T + G, padded
     __shared__ int s_count;
     __shared__ long long s_warp[kTileThreads / 32];
 
@@ -284,7 +290,7 @@ k_groups(int n, int T, int V, int onePerRow, const int *__restrict__ rp, const u
 #pragma unroll 8
     for (int i = threadIdx.x; i < nl; i += blockDim.x) {
         const int a = rp[tbase + i], b = rp[tbase + i + 1];
-        lens[i] = b > a ? b - a : 0;
+        lens[pad32(i)] = b > a ? b - a : 0;
     }
     load_tile_delta(d, delta, tbase, lim);
     __syncthreads();
@@ -317,12 +323,13 @@ k_groups(int n, int T, int V, int onePerRow, const int *__restrict__ rp, const u
     for (int i = threadIdx.x; i < count; i += blockDim.x) {
         const int start = starts[i];
         const int size = d[start];
-        const int *L = lens + start;
+        auto L = [&](int r) { return lens[pad32(start + r)]; };
         unsigned maxlen = 0;
         long long nnz = 0;
         for (int r = 0; r < size; ++r) {
-            maxlen = max(maxlen, (unsigned)L[r]);
-            nnz += L[r];
+            const int l = L(r);
+            maxlen = max(maxlen, (unsigned)l);
+            nnz += l;
         }
         long long C = 0;
         if (maxlen > 0 && onePerRow) {
@@ -342,7 +349,7 @@ k_groups(int n, int T, int V, int onePerRow, const int *__restrict__ rp, const u
                 const unsigned m = 0xffffffffu / mid;
                 int need = 0;
                 for (int r = 0; r < size && need <= G; ++r) {
-                    const unsigned l = (unsigned)L[r];
+                    const unsigned l = (unsigned)L(r);
                     need += l > mid ? (int)ceil_div_by(l, mid, m) : 1;
                 }
                 if (need <= G) hi = mid; else lo = mid + 1;
@@ -355,9 +362,9 @@ k_groups(int n, int T, int V, int onePerRow, const int *__restrict__ rp, const u
         const unsigned Cu = C > 0 && C <= 0x7fffffffLL ? (unsigned)C : 0u;
         const unsigned Cm = Cu ? 0xffffffffu / Cu : 0u;
         for (int r = 0; r < size; ++r) {
-            const unsigned l = (unsigned)L[r];
+            const unsigned l = (unsigned)L(r);
             prefix += (Cu == 0u || l <= Cu) ? 1 : (int)ceil_div_by(l, Cu, Cm);
-            pfx[start + r] = prefix;   // copied out below with coalesced stores
+            pfx[pad32(start + r)] = prefix;   // copied out below with coalesced stores
         }
         // the record keeps the tile index beside the size (size <= 128)
         gscratch[gbase + i] = make_int4(first, size | (k << 8), 0, C <= 0x7fffffffLL ? (int)C : -1);
@@ -371,7 +378,7 @@ k_groups(int n, int T, int V, int onePerRow, const int *__restrict__ rp, const u
         const int rowBegin = starts[0];
         const int rowEnd = starts[count - 1] + d[starts[count - 1]];
         for (int r = rowBegin + (int)threadIdx.x; r < rowEnd; r += blockDim.x)
-            threadsMapping[tbase + r] = pfx[r];
+            threadsMapping[tbase + r] = pfx[pad32(r)];
     }
     // exclusive scan of chunk[i] * G -> slot offset of each group in the tile
     const int per = (count + kTileThreads - 1) / kTileThreads;
@@ -528,12 +535,12 @@ k_fill(long long nGroups, int n_cols, const long long *__restrict__ tileSlotBase
 }
 
 // Dynamic shared memory of k_groups: delta (T), starts (2T), chunk sizes
-// (4T), row lengths (4(T+G)), sub-tile tables (2 S G), sub-tile entries and
-// bases (4 S), threadsMapping of the tile's rows (4(T+G)).
+// (4T), row lengths (4(T+G), padded), sub-tile tables (2 S G), sub-tile
+// entries and bases (4 S), threadsMapping of the tile's rows (4(T+G), padded).
 inline size_t groups_smem(int T, int G) {
     const int S = T / (G > 64 ? G : 64);
     (void)S;
-    return groups_pfx_offset(T, G) + 4 * ((size_t)T + G);
+    return groups_pfx_offset(T, G) + 4 * padded_rows(T, G);
 }
 // Dynamic shared memory of k_tile_prepare: rowPointers (4(T+G+4)), delta
 // (T), sub-tile tables (2 S G).
@@ -647,7 +654,8 @@ extern "C" ARGCSR_API argcsr_status argcsr_create_from_csr(
     const int n = n_rows;
     // tiles of 2048 rows give a 2M-row matrix about 1000 per-tile blocks;
     // very large matrices use longer tiles to keep k_resolve's table short
-    const int T = n <= (1 << 25) ? 2048 : 16384;
+    // (8192 rows: the per-tile kernels' shared memory stays below 143 KB)
+    const int T = n <= (1 << 25) ? 2048 : 8192;
     const int numTiles = (int)(((long long)n + T - 1) / T);
     const size_t es = dtype_size(dtype);
 

@@ -343,6 +343,25 @@ def test_full_size_lognormal_without_adaptive_step(D):
 
 
 @pytest.mark.slow
+def test_more_rows_than_two_to_the_25():
+    # above 2^25 rows the conversion cuts rows into longer tiles (8192)
+    n = (1 << 25) + 4097
+    rng = np.random.default_rng(25)
+    lens = np.ones(n, dtype=np.int64)
+    lens[rng.choice(n, 40, replace=False)] = 300          # a few multi-chunk rows
+    rp = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(lens, out=rp[1:])
+    row_of = np.repeat(np.arange(n, dtype=np.int64), lens)
+    k = np.arange(int(rp[-1]), dtype=np.int64) - np.repeat(rp[:-1], lens)
+    # one entry per row, or a run of 300 consecutive columns (sorted, distinct)
+    cols = np.where(np.repeat(lens, lens) > 1, row_of % (n - 300) + k, (row_of * 7919) % n)
+    del row_of, k
+    A = synth.Csr(n, n, rp.astype(np.int32), cols.astype(np.int32),
+                  rng.standard_normal(int(rp[-1])), "tall")
+    convert_and_check(A, 32, 4, x_seed=3)
+
+
+@pytest.mark.slow
 def test_desired_chunk_size_sweep():
     # the 1..32 sweep of the uneven-rows workload, on a 200k-row sample of it
     A = synth.lognormal_rows(200_000)

@@ -261,7 +261,7 @@ __device__ __forceinline__ unsigned ceil_div_by(unsigned l, unsigned d, unsigned
 // ---------------------------------------------------------------------------
 template <int G>
 __global__ void __launch_bounds__(kTileThreads)
-k_groups(int n, int T, int V, int onePerRow, const int *__restrict__ rp, const uint8_t *__restrict__ delta,
+k_groups(int n, int T, int V, int onePerRow, int gallop, const int *__restrict__ rp, const uint8_t *__restrict__ delta,
          const int *__restrict__ tileEntry, const int *__restrict__ tileGroupBase,
          int4 *__restrict__ gscratch, int *__restrict__ threadsMapping,
          long long *__restrict__ tileSlots, DeviceTotals *tot) {
@@ -344,15 +344,35 @@ k_groups(int n, int T, int V, int onePerRow, const int *__restrict__ rp, const u
                                         (long long)((maxlen + (G - size)) / (G - size + 1)));
             unsigned hi = maxlen;
             lo = max(lo, 1u);
+            // threads needed with chunk size c (stops once above G)
+            auto need = [&](unsigned c) {
+                const unsigned m = 0xffffffffu / c;
+                int t = 0;
+                for (int r = 0; r < size && t <= G; ++r) {
+                    const unsigned l = (unsigned)L(r);
+                    t += l > c ? (int)ceil_div_by(l, c, m) : 1;
+                }
+                return t;
+            };
+            // hi (every row one thread) is always feasible.  When groups hold
+            // few nonzeros (small D) the answer is usually the lower bound or
+            // just above it: probe lo, lo + 1, lo + 2, lo + 4, ... until
+            // feasible, then bisect the last gap.  Otherwise bisect from the
+            // start.  (The choice is per launch, so a warp never runs both.)
+            if (gallop && lo < hi) {
+                unsigned step = 1, below = lo - 1;   // below: largest size known infeasible
+                unsigned c = lo;
+                while (c < hi && need(c) > G) {
+                    below = c;
+                    c = (hi - lo > step) ? lo + step : hi;
+                    step <<= 1;
+                }
+                lo = below + 1;
+                hi = c;
+            }
             while (lo < hi) {
                 const unsigned mid = lo + ((hi - lo) >> 1);
-                const unsigned m = 0xffffffffu / mid;
-                int need = 0;
-                for (int r = 0; r < size && need <= G; ++r) {
-                    const unsigned l = (unsigned)L(r);
-                    need += l > mid ? (int)ceil_div_by(l, mid, m) : 1;
-                }
-                if (need <= G) hi = mid; else lo = mid + 1;
+                if (need(mid) <= G) hi = mid; else lo = mid + 1;
             }
             C = ((long long)lo + V - 1) / V * V;
         }
@@ -569,7 +589,7 @@ struct Kernels {
         {
             TraceScope t("k_groups", s);
             const size_t smem = groups_smem(T, G);
-            k_groups<G><<<numTiles, kTileThreads, smem, s>>>(n, T, V, onePerRow, rp, delta, tileEntry, tileGroupBase,
+            k_groups<G><<<numTiles, kTileThreads, smem, s>>>(n, T, V, onePerRow, limit <= 6LL * G ? 1 : 0, rp, delta, tileEntry, tileGroupBase,
                                                      gscratch, tm, tileSlots, tot);
         }
         {

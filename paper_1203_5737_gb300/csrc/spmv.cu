@@ -35,6 +35,9 @@ namespace {
 #ifndef ARGCSR_SPMV_PREFETCH
 #define ARGCSR_SPMV_PREFETCH 1   // issue batch b+1 before consuming batch b
 #endif
+#ifndef ARGCSR_SPMV_FIXED
+#define ARGCSR_SPMV_FIXED 1      // groups with C <= 8 (V = 1): exact unrolled path
+#endif
 
 // One batch: U blocks of V consecutive elements of this lane's chunk.
 template <typename VT, int V, int U>
@@ -104,6 +107,72 @@ chunk_sum(const int *__restrict__ cols, const VT *__restrict__ vals, const AT *_
     return sum;
 }
 
+// Row map of a G = 32 group from threadsMapping: bit k of `ends` is set when
+// chunk k is the last chunk of a row.
+struct RowEnds {
+    unsigned ends, below;
+    int row;
+    bool owns;
+    __device__ __forceinline__ RowEnds(const int *__restrict__ tm, int first, int size, int lane) {
+        const int end = lane < size ? __ldg(tm + first + lane) : 0;
+        ends = __reduce_or_sync(FULL, lane < size ? 1u << (end - 1) : 0u);
+        below = ends & ((1u << lane) - 1u);
+        row = __popc(below);          // local row of this lane's chunk
+        owns = row < size;            // false for free chunks
+    }
+};
+
+// Segmented tree reduction of the partial sums into the first lane of each
+// row, then the store: a row of t chunks costs t - 1 FP64 adds (FP64
+// throughput on GB300 is about 2 operations per clock per SM, the same
+// budget the FMAs use), in ceil(log2(longest row's chunk count)) steps --
+// none when every row of the group has a single chunk.
+template <typename AT>
+__device__ __forceinline__ void reduce_store(AT sum, const RowEnds &m, int first, int lane,
+                                             const AT *__restrict__ b, AT *__restrict__ y) {
+    const int segStart = m.below ? 32 - __clz(m.below) : 0;
+    const unsigned atOrAbove = m.ends & ~((1u << lane) - 1u);
+    const int segEnd = atOrAbove ? __ffs(atOrAbove) : 0;   // one past the row's last chunk
+    const int maxChunks = __reduce_max_sync(FULL, m.owns ? segEnd - segStart : 0);
+    for (int o = 1; o < maxChunks; o <<= 1) {
+        const AT v = __shfl_down_sync(FULL, sum, o);
+        add_if(sum, v, ((lane - segStart) & (2 * o - 1)) == 0 && lane + o < segEnd);
+    }
+    if (m.owns && lane == segStart) y[first + m.row] = b ? b[first + m.row] - sum : sum;
+}
+
+// A group whose chunk size is exactly CC (V = 1, CC <= 8): the lane issues
+// all its slot loads at once, before threadsMapping is known, then all its
+// x gathers, and spends no multiply-add on slot rows past the chunk.  The
+// multiply-adds run in slot order, as in the batched loop.
+template <int CC, typename VT, typename AT>
+__device__ __forceinline__ void group_fixed(const int4 info, const int *__restrict__ tm,
+                                            const int *__restrict__ cols, const VT *__restrict__ vals,
+                                            const AT *__restrict__ x, const AT *__restrict__ b,
+                                            AT *__restrict__ y, int lane) {
+    const long long base = (long long)info.z + lane;
+    int c[CC];
+    VT v[CC];
+#pragma unroll
+    for (int j = 0; j < CC; ++j) {
+        int cc[1];
+        VT vv[1];
+        ld_stream<int, 1>(cols + base + 32LL * j, cc);
+        ld_stream<VT, 1>(vals + base + 32LL * j, vv);
+        c[j] = cc[0];
+        v[j] = vv[0];
+    }
+    const RowEnds m(tm, info.x, info.y, lane);
+    AT xv[CC];
+#pragma unroll
+    for (int j = 0; j < CC; ++j) xv[j] = (m.owns && c[j] >= 0) ? __ldg(x + c[j]) : AT(0);
+    AT sum = 0;
+#pragma unroll
+    for (int j = 0; j < CC; ++j)
+        if (m.owns && c[j] >= 0) sum = fma((AT)widen(v[j]), xv[j], sum);
+    reduce_store<AT>(sum, m, info.x, lane, b, y);
+}
+
 // G = 32: one warp per group.
 // y = A x, or y = b - A x when b is given (the residual of a solver).
 template <typename VT, typename AT, int V>
@@ -118,31 +187,28 @@ k_spmv_g32(long long nGroups, const int4 *__restrict__ gi, const int *__restrict
     if (g >= nGroups) return;  // warp-uniform
     const int4 info = __ldg(gi + g);  // firstRow, size, offset, chunkSize
     const int first = info.x, size = info.y, C = info.w;
+#if ARGCSR_SPMV_FIXED
+    if constexpr (V == 1) {
+        switch (C) {   // warp-uniform
+            case 1: group_fixed<1>(info, tm, cols, vals, x, b, y, lane); return;
+            case 2: group_fixed<2>(info, tm, cols, vals, x, b, y, lane); return;
+            case 3: group_fixed<3>(info, tm, cols, vals, x, b, y, lane); return;
+            case 4: group_fixed<4>(info, tm, cols, vals, x, b, y, lane); return;
+            case 5: group_fixed<5>(info, tm, cols, vals, x, b, y, lane); return;
+            case 6: group_fixed<6>(info, tm, cols, vals, x, b, y, lane); return;
+            case 7: group_fixed<7>(info, tm, cols, vals, x, b, y, lane); return;
+            case 8: group_fixed<8>(info, tm, cols, vals, x, b, y, lane); return;
+            default: break;
+        }
+    }
+#endif
     const long long base = (long long)info.z + lane * V;
     // the first batch does not depend on threadsMapping: issue it together
     Batch<VT, V, U> B;
     load_batch<VT, V, U>(B, cols + base, vals + base, 32LL * V, 0, C / V, true);
-    const int end = lane < size ? __ldg(tm + first + lane) : 0;
-    // bit k set <=> chunk k is the last chunk of a row
-    const unsigned ends = __reduce_or_sync(FULL, lane < size ? 1u << (end - 1) : 0u);
-    const unsigned below = ends & ((1u << lane) - 1u);
-    const int row = __popc(below);          // local row of this lane's chunk
-    const bool owns = row < size;           // false for free chunks
-    Acc sum = chunk_sum<32, VT, AT, V>(cols, vals, x, base, C, owns, B);
-    // Segmented tree reduction of the partial sums into the first lane of
-    // each row: a row of t chunks costs t - 1 FP64 adds (FP64 throughput on
-    // GB300 is about 2 operations per clock per SM, the same budget the FMAs
-    // use), in ceil(log2(longest row's chunk count)) steps -- none when every
-    // row of the group has a single chunk.
-    const int segStart = below ? 32 - __clz(below) : 0;
-    const unsigned atOrAbove = ends & ~((1u << lane) - 1u);
-    const int segEnd = atOrAbove ? __ffs(atOrAbove) : 0;   // one past the row's last chunk
-    const int maxChunks = __reduce_max_sync(FULL, owns ? segEnd - segStart : 0);
-    for (int o = 1; o < maxChunks; o <<= 1) {
-        const Acc v = __shfl_down_sync(FULL, sum, o);
-        add_if(sum, v, ((lane - segStart) & (2 * o - 1)) == 0 && lane + o < segEnd);
-    }
-    if (owns && lane == segStart) y[first + row] = b ? b[first + row] - sum : sum;
+    const RowEnds m(tm, first, size, lane);
+    Acc sum = chunk_sum<32, VT, AT, V>(cols, vals, x, base, C, m.owns, B);
+    reduce_store<AT>(sum, m, first, lane, b, y);
 }
 
 // G = 64 or 128: one group per G threads, 256 / G groups per block.

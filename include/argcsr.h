@@ -134,6 +134,19 @@ ARGCSR_API argcsr_status argcsr_create_from_csr(
     argcsr_dtype dtype, const argcsr_params *params,
     argcsr_stream_t stream, argcsr_t *out);
 
+/* argcsr_create_from_csr_as -- the same conversion with the values stored
+ * in another type than the input's: in_dtype is the type of d_values,
+ * storage_dtype the handle's.  Supported: the same type (a bit copy, as in
+ * argcsr_create_from_csr), f64 -> f32, f64 -> bf16 and f32 -> bf16, each
+ * rounded to nearest even while the values are copied into their slots;
+ * other pairs return ARGCSR_ENOTSUP.  Sections 2 and 3 leave the value type
+ * open (the paper's kernels are templated on it). */
+ARGCSR_API argcsr_status argcsr_create_from_csr_as(
+    int32_t n_rows, int32_t n_cols, int64_t nnz,
+    const int32_t *d_rowPointers, const int32_t *d_columns, const void *d_values,
+    argcsr_dtype in_dtype, argcsr_dtype storage_dtype, const argcsr_params *params,
+    argcsr_stream_t stream, argcsr_t *out);
+
 /* ---------------------------------------------------------------------------
  * argcsr_spmv -- y = A x on ARG-CSR (Section 4).
  *
@@ -146,6 +159,35 @@ ARGCSR_API argcsr_status argcsr_create_from_csr(
  * ------------------------------------------------------------------------ */
 ARGCSR_API argcsr_status argcsr_spmv(argcsr_t A, const void *d_x, void *d_y,
                                      argcsr_stream_t stream);
+
+/* argcsr_spmv_axpby -- y = alpha A x + beta y (the SpMV of Section 4 with a
+ * scaled update, as iterative solvers use it).  Computed per row in the
+ * accumulation type (f64 for ARGCSR_F64, f32 otherwise; alpha and beta are
+ * rounded to it) as fma(alpha, s, beta * y) with s the row's product; when
+ * beta == 0, y is only written (it may hold anything, NaN included).  Same
+ * arguments and errors as argcsr_spmv. */
+ARGCSR_API argcsr_status argcsr_spmv_axpby(argcsr_t A, double alpha, const void *d_x, double beta,
+                                           void *d_y, argcsr_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * argcsr_set_allocator -- device memory from the caller (for example a
+ * framework's caching allocator) instead of the library's stream-ordered
+ * pool, for every array the library allocates from then on: handles,
+ * conversion scratch, batches, solver and serving workspaces.
+ *   alloc(bytes, stream, ctx) returns device memory usable in stream order
+ *     on `stream`, 256-byte aligned (ARGCSR_EINVAL otherwise), or NULL
+ *     (ARGCSR_ENOMEM);
+ *   free(ptr, stream, ctx) gives it back; the library's last use of it is
+ *     enqueued on `stream`, and the memory must not be reused before that
+ *     stream reaches this point.
+ * Both NULL restores the pool.  Only one of them NULL: ARGCSR_EINVAL.  The
+ * allocator cannot change while memory it handed out (or the pool's) is
+ * still held: ARGCSR_EINVAL.  The callbacks may run on the serving engine's
+ * worker thread.  (Not from the paper: an integration point.)
+ * ------------------------------------------------------------------------ */
+typedef void *(*argcsr_alloc_fn)(size_t bytes, argcsr_stream_t stream, void *ctx);
+typedef void (*argcsr_free_fn)(void *ptr, argcsr_stream_t stream, void *ctx);
+ARGCSR_API argcsr_status argcsr_set_allocator(argcsr_alloc_fn alloc, argcsr_free_fn free_fn, void *ctx);
 
 /* Sizes and byte counts of a handle (host only, no device work). */
 ARGCSR_API argcsr_status argcsr_info(argcsr_t A, argcsr_info_t *out);

@@ -86,7 +86,11 @@ _P, _I32, _I64, _U64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c
 _SIGNATURES = {
     "argcsr_create_from_csr": (ctypes.c_int, [_I32, _I32, _I64, _P, _P, _P, ctypes.c_int,
                                               ctypes.POINTER(argcsr_params), _P, ctypes.POINTER(_P)]),
+    "argcsr_create_from_csr_as": (ctypes.c_int, [_I32, _I32, _I64, _P, _P, _P, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.POINTER(argcsr_params), _P, ctypes.POINTER(_P)]),
     "argcsr_spmv": (ctypes.c_int, [_P, _P, _P, _P]),
+    "argcsr_spmv_axpby": (ctypes.c_int, [_P, ctypes.c_double, _P, ctypes.c_double, _P, _P]),
+    "argcsr_set_allocator": (ctypes.c_int, [_P, _P, _P]),
     "argcsr_info": (ctypes.c_int, [_P, ctypes.POINTER(argcsr_info_t)]),
     "argcsr_export": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "argcsr_device_arrays": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P),
@@ -229,8 +233,57 @@ def argcsr_create_from_csr(n_rows, n_cols, nnz, d_rowPointers, d_columns, d_valu
     return out.value
 
 
+def argcsr_create_from_csr_as(n_rows, n_cols, nnz, d_rowPointers, d_columns, d_values, in_dtype,
+                              storage_dtype, group_size, desired_chunk_size, vec_width=1, stream=0,
+                              one_thread_per_row=0) -> int:
+    """The conversion with values converted from in_dtype to storage_dtype."""
+    p = argcsr_params(group_size, desired_chunk_size, vec_width, int(one_thread_per_row))
+    out = ctypes.c_void_p()
+    st = load_library().argcsr_create_from_csr_as(n_rows, n_cols, nnz, d_rowPointers, d_columns,
+                                                  d_values, in_dtype, storage_dtype, ctypes.byref(p),
+                                                  stream, ctypes.byref(out))
+    _check(st, "argcsr_create_from_csr_as")
+    return out.value
+
+
 def argcsr_spmv(A, d_x, d_y, stream=0) -> None:
     _check(load_library().argcsr_spmv(A, d_x, d_y, stream), "argcsr_spmv")
+
+
+def argcsr_spmv_axpby(A, alpha, d_x, beta, d_y, stream=0) -> None:
+    _check(load_library().argcsr_spmv_axpby(A, alpha, d_x, beta, d_y, stream), "argcsr_spmv_axpby")
+
+
+# callback types of argcsr_set_allocator
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+_allocator_refs = []   # keeps the registered callbacks alive
+
+
+def argcsr_set_allocator(alloc=None, free=None) -> None:
+    """Register Python callables alloc(bytes, stream) -> int pointer and
+    free(ptr, stream); no arguments restores the library's own pool."""
+    if (alloc is None) != (free is None):
+        raise ValueError("give both callbacks or neither")
+    if alloc is None:
+        _check(load_library().argcsr_set_allocator(None, None, None), "argcsr_set_allocator")
+        _allocator_refs.clear()
+        return
+    a = ALLOC_FN(lambda n, s, ctx: alloc(int(n), s or 0) or None)
+    f = FREE_FN(lambda p, s, ctx: free(p, s or 0))
+    _check(load_library().argcsr_set_allocator(ctypes.cast(a, ctypes.c_void_p),
+                                               ctypes.cast(f, ctypes.c_void_p), None),
+           "argcsr_set_allocator")
+    _allocator_refs[:] = [a, f]
+
+
+def use_torch_allocator(device=None) -> None:
+    """Back every device allocation of the library with torch's caching
+    allocator (torch.cuda.caching_allocator_alloc / _delete)."""
+    torch = _torch()
+    dev = torch.cuda.current_device() if device is None else device
+    argcsr_set_allocator(lambda n, s: torch.cuda.caching_allocator_alloc(n, dev, s),
+                         lambda p, s: torch.cuda.caching_allocator_delete(p))
 
 
 def argcsr_info(A) -> argcsr_info_t:
@@ -503,7 +556,9 @@ class ArgCsrMatrix:
 
     @classmethod
     def from_csr(cls, rowPointers, columns, values, n_cols, group_size=32, desired_chunk_size=4,
-                 vec_width=1, stream=None, one_thread_per_row=False):
+                 vec_width=1, stream=None, one_thread_per_row=False, storage_dtype=None):
+        """storage_dtype (a torch dtype) stores the values narrower than
+        given (f64 -> f32 / bf16, f32 -> bf16), rounded to nearest even."""
         torch = _torch()
         _check_cuda("rowPointers", rowPointers, torch.int32)
         _check_cuda("columns", columns, torch.int32)
@@ -512,10 +567,11 @@ class ArgCsrMatrix:
         nnz = columns.numel()
         if values.numel() != nnz:
             raise ValueError("values and columns differ in length")
-        h = argcsr_create_from_csr(n_rows, n_cols, nnz, _ptr(rowPointers), _ptr(columns),
-                                   _ptr(values), _dtype_code(values.dtype), group_size,
-                                   desired_chunk_size, vec_width, _stream(stream),
-                                   int(one_thread_per_row))
+        code = _dtype_code(values.dtype)
+        st_code = code if storage_dtype is None else _dtype_code(storage_dtype)
+        h = argcsr_create_from_csr_as(n_rows, n_cols, nnz, _ptr(rowPointers), _ptr(columns),
+                                      _ptr(values), code, st_code, group_size, desired_chunk_size,
+                                      vec_width, _stream(stream), int(one_thread_per_row))
         return cls(h)
 
     @property
@@ -538,6 +594,15 @@ class ArgCsrMatrix:
                 raise ValueError("out has the wrong length")
         argcsr_spmv(self.handle, _ptr(x), _ptr(out), _stream(stream))
         return out
+
+    def spmv_axpby(self, x, y, alpha=1.0, beta=0.0, stream=None):
+        """y = alpha A x + beta y in place (y not read when beta == 0)."""
+        _check_cuda("x", x, self.vector_dtype)
+        _check_cuda("y", y, self.vector_dtype)
+        if x.numel() != self.n_cols or y.numel() != self.n_rows:
+            raise ValueError("x or y has the wrong length")
+        argcsr_spmv_axpby(self.handle, alpha, _ptr(x), beta, _ptr(y), _stream(stream))
+        return y
 
     def info(self) -> dict:
         return argcsr_info(self.handle).as_dict()

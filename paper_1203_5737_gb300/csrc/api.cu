@@ -51,25 +51,61 @@ static argcsr_status device_pool(cudaMemPool_t *out) {
     return ARGCSR_OK;
 }
 
+// A caller's allocator (argcsr_set_allocator) replaces the pool for every
+// device allocation while it is set.  g_live counts the allocations not yet
+// freed, so the allocator cannot change under memory it has to free.
+struct UserAllocator {
+    argcsr_alloc_fn alloc = nullptr;
+    argcsr_free_fn free = nullptr;
+    void *ctx = nullptr;
+};
+static std::mutex g_alloc_mutex;
+static UserAllocator g_user;
+static int64_t g_live = 0;
+
 argcsr_status pool_alloc(void **p, size_t bytes, cudaStream_t s) {
     *p = nullptr;
     if (bytes == 0) return ARGCSR_OK;
-    cudaMemPool_t pool;
-    argcsr_status st = device_pool(&pool);
-    if (st != ARGCSR_OK) return st;
     // round up so every array starts 256-byte aligned and vector loads of
     // the last slots stay inside the allocation
     bytes = (bytes + 255) & ~size_t(255);
+    std::unique_lock<std::mutex> lock(g_alloc_mutex);
+    const UserAllocator u = g_user;
+    if (u.alloc) {
+        void *q = u.alloc(bytes, reinterpret_cast<argcsr_stream_t>(s), u.ctx);
+        if (!q) {
+            set_error_message("allocator callback returned NULL");
+            return ARGCSR_ENOMEM;
+        }
+        if (reinterpret_cast<uintptr_t>(q) % 256) {
+            u.free(q, reinterpret_cast<argcsr_stream_t>(s), u.ctx);
+            set_error_message("allocator callback returned memory that is not 256-byte aligned");
+            return ARGCSR_EINVAL;
+        }
+        *p = q;
+        ++g_live;
+        return ARGCSR_OK;
+    }
+    lock.unlock();
+    cudaMemPool_t pool;
+    argcsr_status st = device_pool(&pool);
+    if (st != ARGCSR_OK) return st;
     cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, s);
     if (e != cudaSuccess) {
         *p = nullptr;
         return record_cuda(e, "cudaMallocFromPoolAsync");
     }
+    lock.lock();
+    ++g_live;
     return ARGCSR_OK;
 }
 
 void pool_free(void *p, cudaStream_t s) {
-    if (p) cudaFreeAsync(p, s);
+    if (!p) return;
+    std::lock_guard<std::mutex> lock(g_alloc_mutex);
+    if (g_user.free) g_user.free(p, reinterpret_cast<argcsr_stream_t>(s), g_user.ctx);
+    else cudaFreeAsync(p, s);
+    --g_live;
 }
 
 }  // namespace argcsr
@@ -175,6 +211,29 @@ ARGCSR_API argcsr_status argcsr_spmv(argcsr_t A, const void *d_x, void *d_y, arg
     const char *y0 = static_cast<const char *>(d_y), *y1 = y0 + (size_t)A->n_rows * es;
     if (d_x && x0 < y1 && y0 < x1) return ARGCSR_EINVAL;  // x and y overlap
     return launch_spmv(A, d_x, d_y, reinterpret_cast<cudaStream_t>(stream));
+}
+
+ARGCSR_API argcsr_status argcsr_set_allocator(argcsr_alloc_fn alloc, argcsr_free_fn free_fn, void *ctx) {
+    if (!alloc != !free_fn) return ARGCSR_EINVAL;
+    std::lock_guard<std::mutex> lock(g_alloc_mutex);
+    if (g_live != 0) {
+        set_error_message("argcsr_set_allocator: device memory from the current allocator is still held");
+        return ARGCSR_EINVAL;
+    }
+    g_user = UserAllocator{alloc, free_fn, ctx};
+    return ARGCSR_OK;
+}
+
+ARGCSR_API argcsr_status argcsr_spmv_axpby(argcsr_t A, double alpha, const void *d_x, double beta,
+                                           void *d_y, argcsr_stream_t stream) {
+    if (!A) return ARGCSR_EINVAL;
+    if (A->n_rows == 0) return ARGCSR_OK;
+    if (!d_y || (!d_x && A->n_cols > 0)) return ARGCSR_EINVAL;
+    const size_t es = vec_size(A->dtype);
+    const char *x0 = static_cast<const char *>(d_x), *x1 = x0 + (size_t)A->n_cols * es;
+    const char *y0 = static_cast<const char *>(d_y), *y1 = y0 + (size_t)A->n_rows * es;
+    if (d_x && x0 < y1 && y0 < x1) return ARGCSR_EINVAL;  // x and y overlap
+    return launch_spmv_axpby(A, alpha, d_x, beta, d_y, reinterpret_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -38,6 +38,7 @@
 #include <stdio.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "internal.cuh"
 
@@ -463,12 +464,30 @@ k_tile_scan(int numTiles, const long long *__restrict__ tileSlots, long long *__
 // ---------------------------------------------------------------------------
 // 6. Group records and the chunk-wise copy (one warp per group).
 // ---------------------------------------------------------------------------
-template <int G, typename VT, int V>
+
+// A value of the input type in the storage type: a bit copy when the two
+// are the same; otherwise rounded to nearest even (BF16 is kept as its raw
+// 16 bits).
+template <typename VO, typename VI>
+__device__ __forceinline__ VO to_storage(VI v) {
+    if constexpr (std::is_same<VO, VI>::value) return v;
+    else if constexpr (std::is_same<VO, float>::value && std::is_same<VI, double>::value)
+        return __double2float_rn(v);
+    else if constexpr (std::is_same<VO, uint16_t>::value && std::is_same<VI, double>::value)
+        return __bfloat16_as_ushort(__double2bfloat16(v));
+    else {
+        static_assert(std::is_same<VO, uint16_t>::value && std::is_same<VI, float>::value,
+                      "unsupported value conversion");
+        return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+    }
+}
+
+template <int G, typename VT, typename VO, int V>
 __global__ void __launch_bounds__(256)
 k_fill(long long nGroups, int n_cols, const long long *__restrict__ tileSlotBase,
        const int4 *__restrict__ gscratch, const int *__restrict__ rp, const int *__restrict__ colsIn,
        const VT *__restrict__ valsIn, const int *__restrict__ threadsMapping,
-       int4 *__restrict__ groupInfo, int *__restrict__ colsOut, VT *__restrict__ valsOut,
+       int4 *__restrict__ groupInfo, int *__restrict__ colsOut, VO *__restrict__ valsOut,
        DeviceTotals *tot) {
     __shared__ short s_rowOf[8][G];     // chunk -> row of the group (G > 32)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -523,7 +542,7 @@ k_fill(long long nGroups, int n_cols, const long long *__restrict__ tileSlotBase
             const int *cIn = colsIn + src;
             const VT *vIn = valsIn + src;
             int *cOut = colsOut + off + (long long)c * V;
-            VT *vOut = valsOut + off + (long long)c * V;
+            VO *vOut = valsOut + off + (long long)c * V;
             for (int j0 = 0; j0 < C; j0 += 4) {
                 int cc[4];
                 VT vv[4];
@@ -544,7 +563,7 @@ k_fill(long long nGroups, int n_cols, const long long *__restrict__ tileSlotBase
                     if (j < C) {
                         const int at = (j / V) * (G * V) + (j % V);
                         cOut[at] = cc[u];
-                        vOut[at] = vv[u];
+                        vOut[at] = to_storage<VO>(vv[u]);
                     }
                 }
             }
@@ -600,7 +619,7 @@ struct Kernels {
         ARGCSR_CHECK_LAUNCH("conversion structure kernels");
         return ARGCSR_OK;
     }
-    template <typename VT>
+    template <typename VT, typename VO = VT>
     static argcsr_status run_fill(long long nGroups, int V, int n_cols,
                                   const long long *tileSlotBase,
                                   const int4 *gscratch, const int *rp, const int *cols,
@@ -610,16 +629,16 @@ struct Kernels {
         const long long blocks = min((nGroups + 7) / 8, 152LL * 64);
         TraceScope t("k_fill", s);
         const VT *v = static_cast<const VT *>(vals);
-        VT *vo = static_cast<VT *>(valsOut);
+        VO *vo = static_cast<VO *>(valsOut);
         if (V == 1)
-            k_fill<G, VT, 1><<<(unsigned)blocks, 256, 0, s>>>(nGroups, n_cols, tileSlotBase, gscratch, rp,
-                                                              cols, v, tm, gi, colsOut, vo, tot);
+            k_fill<G, VT, VO, 1><<<(unsigned)blocks, 256, 0, s>>>(nGroups, n_cols, tileSlotBase, gscratch, rp,
+                                                                  cols, v, tm, gi, colsOut, vo, tot);
         else if (V == 2)
-            k_fill<G, VT, 2><<<(unsigned)blocks, 256, 0, s>>>(nGroups, n_cols, tileSlotBase, gscratch, rp,
-                                                              cols, v, tm, gi, colsOut, vo, tot);
+            k_fill<G, VT, VO, 2><<<(unsigned)blocks, 256, 0, s>>>(nGroups, n_cols, tileSlotBase, gscratch, rp,
+                                                                  cols, v, tm, gi, colsOut, vo, tot);
         else
-            k_fill<G, VT, 4><<<(unsigned)blocks, 256, 0, s>>>(nGroups, n_cols, tileSlotBase, gscratch, rp,
-                                                              cols, v, tm, gi, colsOut, vo, tot);
+            k_fill<G, VT, VO, 4><<<(unsigned)blocks, 256, 0, s>>>(nGroups, n_cols, tileSlotBase, gscratch, rp,
+                                                                  cols, v, tm, gi, colsOut, vo, tot);
         count_launches(1);
         ARGCSR_CHECK_LAUNCH("k_fill");
         return ARGCSR_OK;
@@ -648,18 +667,37 @@ struct Scratch {
 
 using namespace argcsr;
 
+namespace {
+// input -> storage value types a conversion accepts: the same type, or a
+// narrowing one (f64 -> f32, f64 -> bf16, f32 -> bf16)
+bool conversion_supported(argcsr_dtype in, argcsr_dtype st) {
+    return in == st || (in == ARGCSR_F64 && (st == ARGCSR_F32 || st == ARGCSR_BF16)) ||
+           (in == ARGCSR_F32 && st == ARGCSR_BF16);
+}
+}  // namespace
+
 extern "C" ARGCSR_API argcsr_status argcsr_create_from_csr(
     int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t *d_rowPointers,
     const int32_t *d_columns, const void *d_values, argcsr_dtype dtype, const argcsr_params *params,
     argcsr_stream_t stream, argcsr_t *out) {
+    return argcsr_create_from_csr_as(n_rows, n_cols, nnz, d_rowPointers, d_columns, d_values, dtype,
+                                     dtype, params, stream, out);
+}
+
+extern "C" ARGCSR_API argcsr_status argcsr_create_from_csr_as(
+    int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t *d_rowPointers,
+    const int32_t *d_columns, const void *d_values, argcsr_dtype in_dtype, argcsr_dtype dtype,
+    const argcsr_params *params, argcsr_stream_t stream, argcsr_t *out) {
     if (!out) return ARGCSR_EINVAL;
     *out = nullptr;
+    if (in_dtype != ARGCSR_F64 && in_dtype != ARGCSR_F32 && in_dtype != ARGCSR_BF16) return ARGCSR_EINVAL;
     if (!params || n_rows < 0 || n_cols < 0 || nnz < 0 || nnz > 0x7fffffffLL) return ARGCSR_EINVAL;
     const int G = params->group_size, D = params->desired_chunk_size, V = params->vec_width;
     const int P1 = params->one_thread_per_row;
     if ((G != 32 && G != 64 && G != 128) || D < 1 || (V != 1 && V != 2 && V != 4)) return ARGCSR_EINVAL;
     if (P1 != 0 && P1 != 1) return ARGCSR_EINVAL;
     if (dtype != ARGCSR_F64 && dtype != ARGCSR_F32 && dtype != ARGCSR_BF16) return ARGCSR_EINVAL;
+    if (!conversion_supported(in_dtype, dtype)) return ARGCSR_ENOTSUP;
     if (!d_rowPointers || (nnz > 0 && (!d_columns || !d_values))) return ARGCSR_EINVAL;
     if (n_rows == 0 && nnz != 0) return ARGCSR_EINVAL;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -725,14 +763,22 @@ extern "C" ARGCSR_API argcsr_status argcsr_create_from_csr(
     if ((st = pool_alloc((void **)&A->d_columns, (size_t)A->n_slots * 4, s)) != ARGCSR_OK) return fail(st);
     if ((st = pool_alloc(&A->d_values, (size_t)A->n_slots * es, s)) != ARGCSR_OK) return fail(st);
 
-#define FILL(GG, VT)                                                                             \
-    Kernels<GG>::template run_fill<VT>(A->n_groups, V, n_cols, tileSlotBase,                       \
-                                       gscratch, d_rowPointers, d_columns, d_values,              \
-                                       A->d_threadsMapping, A->d_groupInfo, A->d_columns,         \
-                                       A->d_values, tot, s)
-    if (es == 8) st = G == 32 ? FILL(32, double) : G == 64 ? FILL(64, double) : FILL(128, double);
-    else if (es == 4) st = G == 32 ? FILL(32, float) : G == 64 ? FILL(64, float) : FILL(128, float);
-    else st = G == 32 ? FILL(32, uint16_t) : G == 64 ? FILL(64, uint16_t) : FILL(128, uint16_t);
+#define FILL(GG, VI, VO)                                                                         \
+    Kernels<GG>::template run_fill<VI, VO>(A->n_groups, V, n_cols, tileSlotBase,                   \
+                                           gscratch, d_rowPointers, d_columns, d_values,          \
+                                           A->d_threadsMapping, A->d_groupInfo, A->d_columns,     \
+                                           A->d_values, tot, s)
+#define FILL_G(VI, VO) (G == 32 ? FILL(32, VI, VO) : G == 64 ? FILL(64, VI, VO) : FILL(128, VI, VO))
+    if (in_dtype == dtype) {
+        if (es == 8) st = FILL_G(double, double);
+        else if (es == 4) st = FILL_G(float, float);
+        else st = FILL_G(uint16_t, uint16_t);
+    } else if (in_dtype == ARGCSR_F64) {
+        st = dtype == ARGCSR_F32 ? FILL_G(double, float) : FILL_G(double, uint16_t);
+    } else {
+        st = FILL_G(float, uint16_t);
+    }
+#undef FILL_G
 #undef FILL
     if (st != ARGCSR_OK) return fail(st);
     e = cudaMemcpyAsync(&h, tot, sizeof h, cudaMemcpyDeviceToHost, s);

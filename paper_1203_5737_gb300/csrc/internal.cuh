@@ -80,6 +80,9 @@ inline size_t vec_size(argcsr_dtype t) {  // element size of x and y
 
 // Defined in spmv.cu: launch the ARG-CSR SpMV kernel for a handle.
 argcsr_status launch_spmv(const argcsr_matrix *A, const void *x, void *y, cudaStream_t s);
+// y = alpha A x + beta y (y not read when beta is 0).
+argcsr_status launch_spmv_axpby(const argcsr_matrix *A, double alpha, const void *x, double beta,
+                                void *y, cudaStream_t s);
 // Plain CSR FP64 (vector kernel): y = A x and r = b - A x.
 argcsr_status launch_csr_vector_f64(int32_t n, int32_t n_cols, int64_t nnz, const int32_t *rp,
                                     const int32_t *cols, const double *vals, const double *x,

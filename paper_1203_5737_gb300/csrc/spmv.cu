@@ -107,6 +107,22 @@ chunk_sum(const int *__restrict__ cols, const VT *__restrict__ vals, const AT *_
     return sum;
 }
 
+// What is stored for a row whose product is s: s (SpMV), b - s (the
+// residual of a solver) or alpha s + beta y (y not read when beta is 0).
+// MODE is a compile-time constant, so the plain product's kernel carries
+// none of the others' code.
+template <typename AT>
+struct Epi {
+    const AT *b;
+    AT alpha, beta;
+    template <int MODE>   // 0 product, 1 residual, 2 axpby
+    __device__ __forceinline__ AT apply(AT s, const AT *__restrict__ y, long long r) const {
+        if constexpr (MODE == 0) return s;
+        else if constexpr (MODE == 1) return b[r] - s;
+        else return beta == AT(0) ? alpha * s : fma(alpha, s, beta * y[r]);
+    }
+};
+
 // Row map of a G = 32 group from threadsMapping: bit k of `ends` is set when
 // chunk k is the last chunk of a row.
 struct RowEnds {
@@ -127,9 +143,9 @@ struct RowEnds {
 // throughput on GB300 is about 2 operations per clock per SM, the same
 // budget the FMAs use), in ceil(log2(longest row's chunk count)) steps --
 // none when every row of the group has a single chunk.
-template <typename AT>
+template <int MODE, typename AT>
 __device__ __forceinline__ void reduce_store(AT sum, const RowEnds &m, int first, int lane,
-                                             const AT *__restrict__ b, AT *__restrict__ y) {
+                                             const Epi<AT> &ep, AT *__restrict__ y) {
     const int segStart = m.below ? 32 - __clz(m.below) : 0;
     const unsigned atOrAbove = m.ends & ~((1u << lane) - 1u);
     const int segEnd = atOrAbove ? __ffs(atOrAbove) : 0;   // one past the row's last chunk
@@ -138,17 +154,17 @@ __device__ __forceinline__ void reduce_store(AT sum, const RowEnds &m, int first
         const AT v = __shfl_down_sync(FULL, sum, o);
         add_if(sum, v, ((lane - segStart) & (2 * o - 1)) == 0 && lane + o < segEnd);
     }
-    if (m.owns && lane == segStart) y[first + m.row] = b ? b[first + m.row] - sum : sum;
+    if (m.owns && lane == segStart) y[first + m.row] = ep.template apply<MODE>(sum, y, first + m.row);
 }
 
 // A group whose chunk size is exactly CC (V = 1, CC <= 8): the lane issues
 // all its slot loads at once, before threadsMapping is known, then all its
 // x gathers, and spends no multiply-add on slot rows past the chunk.  The
 // multiply-adds run in slot order, as in the batched loop.
-template <int CC, typename VT, typename AT>
+template <int CC, int MODE, typename VT, typename AT>
 __device__ __forceinline__ void group_fixed(const int4 info, const int *__restrict__ tm,
                                             const int *__restrict__ cols, const VT *__restrict__ vals,
-                                            const AT *__restrict__ x, const AT *__restrict__ b,
+                                            const AT *__restrict__ x, const Epi<AT> &ep,
                                             AT *__restrict__ y, int lane) {
     const long long base = (long long)info.z + lane;
     int c[CC];
@@ -170,16 +186,19 @@ __device__ __forceinline__ void group_fixed(const int4 info, const int *__restri
 #pragma unroll
     for (int j = 0; j < CC; ++j)
         if (m.owns && c[j] >= 0) sum = fma((AT)widen(v[j]), xv[j], sum);
-    reduce_store<AT>(sum, m, info.x, lane, b, y);
+    reduce_store<MODE, AT>(sum, m, info.x, lane, ep, y);
 }
 
 // G = 32: one warp per group.
 // y = A x, or y = b - A x when b is given (the residual of a solver).
-template <typename VT, typename AT, int V>
-__global__ void __launch_bounds__(256)
+// Register budgets: 32 with FP32 accumulation, so that 64 warps fit on an
+// SM (the gathers need every warp in flight), 40 with FP64 (48 warps; 51 for
+// V = 4, whose wider loads need more).
+template <typename VT, typename AT, int V, int MODE>
+__global__ void __launch_bounds__(256, sizeof(AT) == 4 ? 8 : (V == 4 ? 5 : 6))
 k_spmv_g32(long long nGroups, const int4 *__restrict__ gi, const int *__restrict__ tm,
            const int *__restrict__ cols, const VT *__restrict__ vals, const AT *__restrict__ x,
-           const AT *__restrict__ b, AT *__restrict__ y) {
+           const Epi<AT> ep, AT *__restrict__ y) {
     using Acc = AT;
     constexpr int U = (ARGCSR_SPMV_ELEMS + V - 1) / V;
     const int lane = threadIdx.x & 31;
@@ -190,14 +209,14 @@ k_spmv_g32(long long nGroups, const int4 *__restrict__ gi, const int *__restrict
 #if ARGCSR_SPMV_FIXED
     if constexpr (V == 1) {
         switch (C) {   // warp-uniform
-            case 1: group_fixed<1>(info, tm, cols, vals, x, b, y, lane); return;
-            case 2: group_fixed<2>(info, tm, cols, vals, x, b, y, lane); return;
-            case 3: group_fixed<3>(info, tm, cols, vals, x, b, y, lane); return;
-            case 4: group_fixed<4>(info, tm, cols, vals, x, b, y, lane); return;
-            case 5: group_fixed<5>(info, tm, cols, vals, x, b, y, lane); return;
-            case 6: group_fixed<6>(info, tm, cols, vals, x, b, y, lane); return;
-            case 7: group_fixed<7>(info, tm, cols, vals, x, b, y, lane); return;
-            case 8: group_fixed<8>(info, tm, cols, vals, x, b, y, lane); return;
+            case 1: group_fixed<1, MODE>(info, tm, cols, vals, x, ep, y, lane); return;
+            case 2: group_fixed<2, MODE>(info, tm, cols, vals, x, ep, y, lane); return;
+            case 3: group_fixed<3, MODE>(info, tm, cols, vals, x, ep, y, lane); return;
+            case 4: group_fixed<4, MODE>(info, tm, cols, vals, x, ep, y, lane); return;
+            case 5: group_fixed<5, MODE>(info, tm, cols, vals, x, ep, y, lane); return;
+            case 6: group_fixed<6, MODE>(info, tm, cols, vals, x, ep, y, lane); return;
+            case 7: group_fixed<7, MODE>(info, tm, cols, vals, x, ep, y, lane); return;
+            case 8: group_fixed<8, MODE>(info, tm, cols, vals, x, ep, y, lane); return;
             default: break;
         }
     }
@@ -208,15 +227,15 @@ k_spmv_g32(long long nGroups, const int4 *__restrict__ gi, const int *__restrict
     load_batch<VT, V, U>(B, cols + base, vals + base, 32LL * V, 0, C / V, true);
     const RowEnds m(tm, first, size, lane);
     Acc sum = chunk_sum<32, VT, AT, V>(cols, vals, x, base, C, m.owns, B);
-    reduce_store<AT>(sum, m, first, lane, b, y);
+    reduce_store<MODE, AT>(sum, m, first, lane, ep, y);
 }
 
 // G = 64 or 128: one group per G threads, 256 / G groups per block.
-template <int G, typename VT, typename AT, int V>
+template <int G, typename VT, typename AT, int V, int MODE>
 __global__ void __launch_bounds__(256)
 k_spmv_block(long long nGroups, const int4 *__restrict__ gi, const int *__restrict__ tm,
              const int *__restrict__ cols, const VT *__restrict__ vals, const AT *__restrict__ x,
-             const AT *__restrict__ b, AT *__restrict__ y) {
+             const Epi<AT> ep, AT *__restrict__ y) {
     using Acc = AT;
     constexpr int GPB = 256 / G;
     __shared__ Acc partial[256];
@@ -245,12 +264,12 @@ k_spmv_block(long long nGroups, const int4 *__restrict__ gi, const int *__restri
     if (c < size) {
         Acc s = partial[sub * G + begin];
         for (int k = begin + 1; k < end; ++k) s += partial[sub * G + k];
-        y[first + c] = b ? b[first + c] - s : s;
+        y[first + c] = ep.template apply<MODE>(s, y, first + c);
     }
 }
 
-template <typename VT, typename AT, int V>
-argcsr_status launch_typed(const argcsr_matrix *A, const void *x, const void *b, void *y,
+template <typename VT, typename AT, int V, int MODE>
+argcsr_status launch_typed(const argcsr_matrix *A, const void *x, const Epi<AT> &ep, void *y,
                            cudaStream_t s) {
     const long long ng = A->n_groups;
     const auto *gi = A->d_groupInfo;
@@ -258,27 +277,32 @@ argcsr_status launch_typed(const argcsr_matrix *A, const void *x, const void *b,
     const auto *cols = A->d_columns;
     const auto *vals = static_cast<const VT *>(A->d_values);
     const auto *xx = static_cast<const AT *>(x);
-    const auto *bb = static_cast<const AT *>(b);
     auto *yy = static_cast<AT *>(y);
-    TraceScope t(A->G == 32 ? (b ? "k_residual_g32" : "k_spmv_g32")
-                            : (b ? "k_residual_block" : "k_spmv_block"), s);
+    static const char *names[2][3] = {{"k_spmv_g32", "k_residual_g32", "k_spmv_axpby_g32"},
+                                      {"k_spmv_block", "k_residual_block", "k_spmv_axpby_block"}};
+    TraceScope t(names[A->G == 32 ? 0 : 1][MODE], s);
     switch (A->G) {
-        case 32: k_spmv_g32<VT, AT, V><<<(unsigned)((ng + 7) / 8), 256, 0, s>>>(ng, gi, tm, cols, vals, xx, bb, yy); break;
-        case 64: k_spmv_block<64, VT, AT, V><<<(unsigned)((ng + 3) / 4), 256, 0, s>>>(ng, gi, tm, cols, vals, xx, bb, yy); break;
-        default: k_spmv_block<128, VT, AT, V><<<(unsigned)((ng + 1) / 2), 256, 0, s>>>(ng, gi, tm, cols, vals, xx, bb, yy); break;
+        case 32: k_spmv_g32<VT, AT, V, MODE><<<(unsigned)((ng + 7) / 8), 256, 0, s>>>(ng, gi, tm, cols, vals, xx, ep, yy); break;
+        case 64: k_spmv_block<64, VT, AT, V, MODE><<<(unsigned)((ng + 3) / 4), 256, 0, s>>>(ng, gi, tm, cols, vals, xx, ep, yy); break;
+        default: k_spmv_block<128, VT, AT, V, MODE><<<(unsigned)((ng + 1) / 2), 256, 0, s>>>(ng, gi, tm, cols, vals, xx, ep, yy); break;
     }
     count_launches(1);
     ARGCSR_CHECK_LAUNCH("argcsr_spmv kernel");
     return ARGCSR_OK;
 }
 
-template <typename VT, typename AT>
-argcsr_status launch_v(const argcsr_matrix *A, const void *x, const void *b, void *y, cudaStream_t s) {
+template <typename VT, typename AT, int MODE>
+argcsr_status launch_v(const argcsr_matrix *A, const void *x, const Epi<AT> &ep, void *y, cudaStream_t s) {
     switch (A->V) {
-        case 1: return launch_typed<VT, AT, 1>(A, x, b, y, s);
-        case 2: return launch_typed<VT, AT, 2>(A, x, b, y, s);
-        default: return launch_typed<VT, AT, 4>(A, x, b, y, s);
+        case 1: return launch_typed<VT, AT, 1, MODE>(A, x, ep, y, s);
+        case 2: return launch_typed<VT, AT, 2, MODE>(A, x, ep, y, s);
+        default: return launch_typed<VT, AT, 4, MODE>(A, x, ep, y, s);
     }
+}
+
+template <typename AT>
+Epi<AT> epi(const void *b = nullptr, double alpha = 1.0, double beta = 0.0) {
+    return Epi<AT>{static_cast<const AT *>(b), (AT)alpha, (AT)beta};
 }
 
 }  // namespace
@@ -286,9 +310,19 @@ argcsr_status launch_v(const argcsr_matrix *A, const void *x, const void *b, voi
 argcsr_status launch_spmv(const argcsr_matrix *A, const void *x, void *y, cudaStream_t s) {
     if (A->n_groups == 0) return ARGCSR_OK;   // no rows
     switch (A->dtype) {
-        case ARGCSR_F64: return launch_v<double, double>(A, x, nullptr, y, s);
-        case ARGCSR_F32: return launch_v<float, float>(A, x, nullptr, y, s);
-        default: return launch_v<uint16_t, float>(A, x, nullptr, y, s);
+        case ARGCSR_F64: return launch_v<double, double, 0>(A, x, epi<double>(), y, s);
+        case ARGCSR_F32: return launch_v<float, float, 0>(A, x, epi<float>(), y, s);
+        default: return launch_v<uint16_t, float, 0>(A, x, epi<float>(), y, s);
+    }
+}
+
+argcsr_status launch_spmv_axpby(const argcsr_matrix *A, double alpha, const void *x, double beta,
+                                void *y, cudaStream_t s) {
+    if (A->n_groups == 0) return ARGCSR_OK;
+    switch (A->dtype) {
+        case ARGCSR_F64: return launch_v<double, double, 2>(A, x, epi<double>(nullptr, alpha, beta), y, s);
+        case ARGCSR_F32: return launch_v<float, float, 2>(A, x, epi<float>(nullptr, alpha, beta), y, s);
+        default: return launch_v<uint16_t, float, 2>(A, x, epi<float>(nullptr, alpha, beta), y, s);
     }
 }
 
@@ -296,9 +330,9 @@ argcsr_status launch_residual_f64(const argcsr_matrix *A, const double *b, const
                                   double *r, cudaStream_t s) {
     if (A->n_groups == 0) return ARGCSR_OK;
     switch (A->dtype) {
-        case ARGCSR_F64: return launch_v<double, double>(A, x, b, r, s);
-        case ARGCSR_F32: return launch_v<float, double>(A, x, b, r, s);
-        default: return launch_v<uint16_t, double>(A, x, b, r, s);
+        case ARGCSR_F64: return launch_v<double, double, 1>(A, x, epi<double>(b), r, s);
+        case ARGCSR_F32: return launch_v<float, double, 1>(A, x, epi<double>(b), r, s);
+        default: return launch_v<uint16_t, double, 1>(A, x, epi<double>(b), r, s);
     }
 }
 

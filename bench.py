@@ -1032,6 +1032,48 @@ def run_ncu_case(which):
     from paper_1203_5737_gb300 import build
     build.build()
     s = torch.cuda.current_stream().cuda_stream
+    if which == "cg":
+        # one refinement step of the FP32-storage CG on the 160^3 Poisson
+        # matrix: residual, norms, 16 inner iterations (SpMV and the three
+        # vector kernels), correction -- about 0.5 GB on the device
+        A = synth.laplacian_3d(160)
+        rp = torch.from_numpy(A.rowPointers).cuda()
+        cols = torch.from_numpy(A.columns).cuda()
+        v64 = torch.from_numpy(A.values).cuda()
+        h = api.argcsr_create_from_csr(A.n_rows, A.n_cols, A.nnz, rp.data_ptr(), cols.data_ptr(),
+                                       v64.float().data_ptr(), api.ARGCSR_F32, GROUP_SIZE, 8, 1, s)
+        b = torch.rand(A.n_rows, dtype=torch.float64, device="cuda")
+        x = torch.zeros_like(b)
+        api.argcsr_cg_solve(h, None, b.data_ptr(), x.data_ptr(), tol=1e-30, max_iters=16,
+                            max_outer=1, check_every=16, stream=s)
+        torch.cuda.synchronize()
+        api.argcsr_destroy(h, s)
+        print(f"ncu case {which}: ok")
+        return
+    if which == "batch":
+        # 512 matrices of the 4096-matrix batch recipe, one launch each of
+        # k = 1 and k = 16 -- about 0.6 GB on the device
+        mats = synth.diag_dominant_batch(512, seed=0, workers=min(16, os.cpu_count() or 1))
+        handles, keep = [], []
+        for A in mats:
+            t = (torch.from_numpy(A.rowPointers).cuda(), torch.from_numpy(A.columns).cuda(),
+                 torch.from_numpy(A.values.astype(np.float32)).cuda())
+            keep.append(t)
+            handles.append(api.argcsr_create_from_csr(A.n_rows, A.n_cols, A.nnz, t[0].data_ptr(),
+                                                      t[1].data_ptr(), t[2].data_ptr(), api.ARGCSR_F32,
+                                                      GROUP_SIZE, 4, 1, s))
+        B = api.argcsr_batch_create(handles, s)
+        info = api.argcsr_batch_info(B)
+        for k in (1, 16):
+            X = torch.rand((info["total_cols"], k), dtype=torch.float32, device="cuda")
+            Y = torch.empty((info["total_rows"], k), dtype=torch.float32, device="cuda")
+            api.argcsr_batch_spmm(B, k, X.data_ptr(), Y.data_ptr(), s)
+        torch.cuda.synchronize()
+        api.argcsr_batch_destroy(B, s)
+        for h in handles:
+            api.argcsr_destroy(h, s)
+        print(f"ncu case {which}: ok")
+        return
     if which == "bench":
         mats = [(synth.workload(name)[0], D) for name, D in MATRICES]
     else:
@@ -1061,7 +1103,7 @@ def main(argv=None):
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-sweep", action="store_true", help="skip the desiredChunkSize sweep")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
-    p.add_argument("--ncu-case", choices=("small", "bench"),
+    p.add_argument("--ncu-case", choices=("small", "bench", "cg", "batch"),
                    help="run a short untimed launch sequence for ncu, then exit")
     p.add_argument("--workload", choices=("uneven_fp64", "cg_poisson160", "batched4096", "serving"),
                    default="uneven_fp64",

@@ -28,7 +28,7 @@ namespace argcsr {
 namespace {
 
 constexpr int kVecBlocks = 152 * 8;  // largest grid of the vector kernels (= partials)
-constexpr int kUnroll = 4;           // independent elements per thread per step
+constexpr int kUnroll = 16;          // independent elements per thread per step
 constexpr int kVecThreads = 256;
 
 // Grid of the vector kernels for n elements: one block per kUnroll * 256
@@ -50,21 +50,23 @@ struct CgState {
     unsigned pad;
 };
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
 // Sum of v over the block (valid in thread 0).
-__device__ __forceinline__ double block_sum(double v) {
-    __shared__ double sh[kVecThreads / 32];
+template <typename T>
+__device__ __forceinline__ T block_sum(T v) {
+    __shared__ T sh[kVecThreads / 32];
     v = warp_sum(v);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
     __syncthreads();
-    double t = 0;
+    T t = 0;
     if (threadIdx.x < 32) {
-        t = threadIdx.x < kVecThreads / 32 ? sh[threadIdx.x] : 0.0;
+        t = threadIdx.x < kVecThreads / 32 ? sh[threadIdx.x] : T(0);
         t = warp_sum(t);
     }
     __syncthreads();
@@ -73,9 +75,13 @@ __device__ __forceinline__ double block_sum(double v) {
 
 // Every block contributes `partial`; returns true in thread 0 of the last
 // block to finish, with the sum of all partials (in block order) in *total.
-__device__ bool last_block_total(double partial, double *partials, unsigned *counter, double *total) {
+// Within a block the sum is taken in the partial's own type (FP32 for the
+// FP32 inner solve: on GB300 an FP64 add costs 32 times an FP32 one), across
+// blocks in FP64.
+template <typename T>
+__device__ bool last_block_total(T partial, double *partials, unsigned *counter, double *total) {
     __shared__ bool s_last;
-    const double bsum = block_sum(partial);
+    const double bsum = (double)block_sum<T>(partial);
     if (threadIdx.x == 0) {
         partials[blockIdx.x] = bsum;
         __threadfence();
@@ -86,7 +92,7 @@ __device__ bool last_block_total(double partial, double *partials, unsigned *cou
     __threadfence();
     double t = 0;
     for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += ((volatile double *)partials)[i];
-    t = block_sum(t);
+    t = block_sum<double>(t);
     if (threadIdx.x == 0) {
         *total = t;
         *counter = 0;  // ready for the next reduction
@@ -115,7 +121,7 @@ k_cg_alpha(const WT *__restrict__ p, const WT *__restrict__ q, long long n, doub
     WT acc = 0;
     FOR_EACH_ELEMENT(n, acc = fma(p[i], q[i], acc));
     double pq;
-    if (last_block_total((double)acc, partials, &S->counter, &pq))
+    if (last_block_total<WT>(acc, partials, &S->counter, &pq))
         S->alpha = pq != 0.0 ? S->rho / pq : 0.0;
 }
 
@@ -133,7 +139,7 @@ k_cg_update(WT *__restrict__ x, WT *__restrict__ r, const WT *__restrict__ p,
         acc = fma(ri, ri, acc);
     });
     double rho_new;
-    if (last_block_total((double)acc, partials, &S->counter, &rho_new)) {
+    if (last_block_total<WT>(acc, partials, &S->counter, &rho_new)) {
         S->beta = S->rho != 0.0 ? rho_new / S->rho : 0.0;
         S->rho = rho_new;
     }
@@ -152,7 +158,7 @@ k_norm2_f64(const double *__restrict__ v, long long n, double *partials, CgState
     double acc = 0;
     FOR_EACH_ELEMENT(n, acc = fma(v[i], v[i], acc));
     double t;
-    if (last_block_total(acc, partials, &S->counter, &t)) {
+    if (last_block_total<double>(acc, partials, &S->counter, &t)) {
         if (which == 0) S->norm2 = t; else S->bnorm2 = t;
     }
 }
@@ -172,7 +178,7 @@ k_ir_start(const double *__restrict__ r64, WT *__restrict__ r, WT *__restrict__ 
         acc = fma(ri, ri, acc);
     });
     double t;
-    if (last_block_total((double)acc, partials, &S->counter, &t)) {
+    if (last_block_total<WT>(acc, partials, &S->counter, &t)) {
         S->rho = t;
         S->rho0 = t;
     }

@@ -126,7 +126,8 @@ typedef struct {
  * The call synchronises `stream` twice (to size the output and to return the
  * validation status) and returns only when the handle is complete.  The
  * handle owns its device arrays (allocated from a stream-ordered pool owned
- * by this library) until argcsr_destroy.  *out is set to NULL on error.
+ * by this library, or from the caller's allocator, see argcsr_set_allocator)
+ * until argcsr_destroy.  *out is set to NULL on error.
  * ------------------------------------------------------------------------ */
 ARGCSR_API argcsr_status argcsr_create_from_csr(
     int32_t n_rows, int32_t n_cols, int64_t nnz,

@@ -80,6 +80,20 @@ inline size_t vec_size(argcsr_dtype t) {  // element size of x and y
 
 // Defined in spmv.cu: launch the ARG-CSR SpMV kernel for a handle.
 argcsr_status launch_spmv(const argcsr_matrix *A, const void *x, void *y, cudaStream_t s);
+// One matrix of a batch (spmm.cu builds the array on the device).
+struct BatchDesc {
+    const int4 *gi;
+    const int *tm;
+    const int *cols;
+    const void *vals;
+    long long rowBase;   // first row of this matrix in the packed Y
+    long long colBase;   // first row of this matrix in the packed X
+};
+// y = A x for every matrix of a batch (k = 1, G = 32, V = 1), one warp per
+// group of the concatenated group list (spmv.cu).
+argcsr_status launch_batch_spmv(const BatchDesc *desc, const long long *groupPrefix, int nMat,
+                                long long totalGroups, argcsr_dtype dtype, const void *X, void *Y,
+                                cudaStream_t s);
 // y = alpha A x + beta y (y not read when beta is 0).
 argcsr_status launch_spmv_axpby(const argcsr_matrix *A, double alpha, const void *x, double beta,
                                 void *y, cudaStream_t s);

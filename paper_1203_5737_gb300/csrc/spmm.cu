@@ -38,15 +38,6 @@ struct argcsr_graph {
 namespace argcsr {
 namespace {
 
-struct BatchDesc {
-    const int4 *gi;
-    const int *tm;
-    const int *cols;
-    const void *vals;
-    long long rowBase;   // first row of this matrix in the packed Y
-    long long colBase;   // first row of this matrix in the packed X
-};
-
 // k values of row `col` of X (row-major, leading dimension ld).
 template <typename AT, int K, bool VEC>
 __device__ __forceinline__ void load_x_row(const AT *__restrict__ row, AT (&xv)[K]) {
@@ -463,6 +454,9 @@ argcsr_status launch_spmm(const argcsr_matrix *A, int k, const void *X, long lon
 
 argcsr_status launch_batch(const argcsr_batch *B, int k, const void *X, void *Y, cudaStream_t s) {
     if (B->total_groups == 0) return ARGCSR_OK;
+    if (k == 1 && B->V == 1)   // one warp per group, the single-matrix product's code
+        return launch_batch_spmv(static_cast<const BatchDesc *>(B->d_desc), B->d_groupPrefix, B->count,
+                                 B->total_groups, B->dtype, X, Y, s);
     TraceScope t("k_batch_spmm_g32", s);
     argcsr_status st;
     switch (B->dtype) {

@@ -305,7 +305,86 @@ Epi<AT> epi(const void *b = nullptr, double alpha = 1.0, double beta = 0.0) {
     return Epi<AT>{static_cast<const AT *>(b), (AT)alpha, (AT)beta};
 }
 
+// Every group of a batch of matrices, one warp per group as in k_spmv_g32
+// (k = 1, V = 1).  A block's 8 groups are consecutive in the concatenated
+// list, so one binary search over the matrices' group prefix per block
+// finds the first one's matrix; a warp walks forward from there.
+template <typename VT, typename AT>
+__global__ void __launch_bounds__(256, sizeof(AT) == 4 ? 8 : 6)
+k_batch_spmv_g32(const BatchDesc *__restrict__ desc, const long long *__restrict__ groupPrefix,
+                 int nMat, long long totalGroups, const AT *__restrict__ X, AT *__restrict__ Y) {
+    __shared__ int s_m;
+    const long long g0 = (long long)blockIdx.x * 8;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = nMat - 1;   // last m with groupPrefix[m] <= g0
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(groupPrefix + mid) <= g0) lo = mid; else hi = mid - 1;
+        }
+        s_m = lo;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const long long g = g0 + (threadIdx.x >> 5);
+    if (g >= totalGroups) return;   // warp-uniform
+    int m = s_m;
+    while (g >= __ldg(groupPrefix + m + 1)) ++m;
+    const BatchDesc d = desc[m];
+    const int4 info = __ldg(d.gi + (g - __ldg(groupPrefix + m)));
+    const int *tm = d.tm, *cols = d.cols;
+    const VT *vals = static_cast<const VT *>(d.vals);
+    const AT *x = X + d.colBase;
+    AT *y = Y + d.rowBase;
+    const Epi<AT> ep{nullptr, AT(1), AT(0)};
+    switch (info.w) {   // warp-uniform
+        case 1: group_fixed<1, 0>(info, tm, cols, vals, x, ep, y, lane); return;
+        case 2: group_fixed<2, 0>(info, tm, cols, vals, x, ep, y, lane); return;
+        case 3: group_fixed<3, 0>(info, tm, cols, vals, x, ep, y, lane); return;
+        case 4: group_fixed<4, 0>(info, tm, cols, vals, x, ep, y, lane); return;
+        case 5: group_fixed<5, 0>(info, tm, cols, vals, x, ep, y, lane); return;
+        case 6: group_fixed<6, 0>(info, tm, cols, vals, x, ep, y, lane); return;
+        case 7: group_fixed<7, 0>(info, tm, cols, vals, x, ep, y, lane); return;
+        case 8: group_fixed<8, 0>(info, tm, cols, vals, x, ep, y, lane); return;
+        default: break;
+    }
+    constexpr int U = ARGCSR_SPMV_ELEMS;
+    const long long base = (long long)info.z + lane;
+    Batch<VT, 1, U> B;
+    load_batch<VT, 1, U>(B, cols + base, vals + base, 32LL, 0, info.w, true);
+    const RowEnds rm(tm, info.x, info.y, lane);
+    const AT sum = chunk_sum<32, VT, AT, 1>(cols, vals, x, base, info.w, rm.owns, B);
+    reduce_store<0, AT>(sum, rm, info.x, lane, ep, y);
+}
+
 }  // namespace
+
+argcsr_status launch_batch_spmv(const BatchDesc *desc, const long long *groupPrefix, int nMat,
+                                long long totalGroups, argcsr_dtype dtype, const void *X, void *Y,
+                                cudaStream_t s) {
+    if (totalGroups == 0) return ARGCSR_OK;
+    const unsigned blocks = (unsigned)((totalGroups + 7) / 8);
+    TraceScope t("k_batch_spmv_g32", s);
+    switch (dtype) {
+        case ARGCSR_F64:
+            k_batch_spmv_g32<double, double><<<blocks, 256, 0, s>>>(desc, groupPrefix, nMat, totalGroups,
+                                                                   static_cast<const double *>(X),
+                                                                   static_cast<double *>(Y));
+            break;
+        case ARGCSR_F32:
+            k_batch_spmv_g32<float, float><<<blocks, 256, 0, s>>>(desc, groupPrefix, nMat, totalGroups,
+                                                                 static_cast<const float *>(X),
+                                                                 static_cast<float *>(Y));
+            break;
+        default:
+            k_batch_spmv_g32<uint16_t, float><<<blocks, 256, 0, s>>>(desc, groupPrefix, nMat, totalGroups,
+                                                                    static_cast<const float *>(X),
+                                                                    static_cast<float *>(Y));
+            break;
+    }
+    count_launches(1);
+    ARGCSR_CHECK_LAUNCH("k_batch_spmv_g32");
+    return ARGCSR_OK;
+}
 
 argcsr_status launch_spmv(const argcsr_matrix *A, const void *x, void *y, cudaStream_t s) {
     if (A->n_groups == 0) return ARGCSR_OK;   // no rows

@@ -205,6 +205,26 @@ def kernel_source_digest(kernel):
     return h.hexdigest()[:16]
 
 
+def ncu_limits(kernel):
+    """Unit utilisation of `kernel` from profiles/limits.txt (same digest
+    rule as the traffic), as {metric: {"laplace3d_128_like": %, "lognormal_like": %}}."""
+    if kernel not in KERNEL_SOURCES:
+        return None
+    digest = kernel_source_digest(kernel)
+    out = {}
+    try:
+        with open(os.path.join(ROOT, "profiles", "limits.txt")) as f:
+            for line in f:
+                if line.startswith("#") or not line.strip():
+                    continue
+                k, metric, lap, logn, dig = line.split()[:5]
+                if k == kernel and dig == digest:
+                    out[metric] = {"laplacian": float(lap), "lognormal": float(logn)}
+    except OSError:
+        return None
+    return out or None
+
+
 def ncu_traffic(kernel):
     """DRAM bytes per launch from profiles/traffic.txt, if they were taken on
     the current sources of that kernel (else None)."""
@@ -327,7 +347,8 @@ def run_ours(args):
                 "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": traffic, "peak_source": peak_kind,
                 "bytes_per_launch": round(kbytes / launches_k),
-                "avg_launch_us": round(ms_k * 1e3 / launches_k, 2)}
+                "avg_launch_us": round(ms_k * 1e3 / launches_k, 2),
+                "other_limits_ncu": ncu_limits(dominant)}
     total_traced = sum(v[1] for v in trace.values())
     kernels = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / total_traced, 4)}
                for k, v in sorted(trace.items(), key=lambda kv: -kv[1][1])}

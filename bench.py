@@ -419,6 +419,44 @@ def run_ours(args):
             best_step = min(rows, key=lambda d: rows[d]["spmv_us"] + rows[d]["convert_us"])
             d_sweep[m.name] = {"best_spmv_D": best_spmv, "best_step_D": best_step, "by_D": rows}
 
+    # the other matrix families (banded, block-structured, power-law): SpMV
+    # with the layout the autotuner picks (G 32 / 64 / 128, D over its
+    # candidates: a row gets at most G threads, which matters for rows of
+    # tens of thousands of entries)
+    families = {}
+    if not args.no_sweep:
+        for fname in synth.FAMILIES:
+            A = synth.family(fname)
+            rp = torch.from_numpy(A.rowPointers).to(dev)
+            cols = torch.from_numpy(A.columns).to(dev)
+            vals = torch.from_numpy(A.values).to(dev)
+            x = torch.from_numpy(synth.uniform_vector(A.n_cols, 2)).to(dev)
+            y = torch.empty(A.n_rows, dtype=torch.float64, device=dev)
+            (G, D, V, _), _ = api.argcsr_autotune(A.n_rows, A.n_cols, A.nnz, rp.data_ptr(), cols.data_ptr(),
+                                                  vals.data_ptr(), api.ARGCSR_F64, 1, 7, 5, s)
+            h = api.argcsr_create_from_csr(A.n_rows, A.n_cols, A.nnz, rp.data_ptr(), cols.data_ptr(),
+                                           vals.data_ptr(), api.ARGCSR_F64, G, D, V, s)
+            info = api.argcsr_info(h)
+            nbytes = spmv_bytes(A.n_rows, A.n_cols, A.nnz, info.n_groups)
+            r = _time_gbs(torch, stream, lambda: api.argcsr_spmv(h, x.data_ptr(), y.data_ptr(), s), nbytes, 20)
+            api.argcsr_destroy(h, s)
+            cb = csr_spmv_bytes(A.n_rows, A.n_cols, A.nnz)
+            csr = {}
+            for variant, key in ((1, "csr_vector"), (0, "csr_scalar")):
+                csr[key] = _time_gbs(torch, stream, lambda: api.argcsr_baseline_csr_spmv(
+                    A.n_rows, A.n_cols, A.nnz, rp.data_ptr(), cols.data_ptr(), vals.data_ptr(),
+                    api.ARGCSR_F64, variant, x.data_ptr(), y.data_ptr(), s), cb, 20)
+            try:
+                Acsr = torch.sparse_csr_tensor(rp, cols, vals, size=(A.n_rows, A.n_cols))
+                csr["cusparse"] = _time_gbs(torch, stream, lambda: torch.mv(Acsr, x), cb, 20)
+            except Exception as exc:  # report, do not fail the bench
+                csr["cusparse"] = {"error": str(exc)[:120]}
+            families[fname] = {"n": A.n_rows, "nnz": A.nnz, "G": G, "D": D,
+                               "slots_per_nnz": round(info.n_slots / A.nnz, 4),
+                               "us": r["us"], "gbs": r["gbs"], "frac": round(r["gbs"] / peak, 4),
+                               "gflops": round(2 * A.nnz / (r["us"] * 1e-6) / 1e9, 1), "baselines": csr}
+            del rp, cols, vals, x, y
+
     # what the adaptive step gains: the same SpMV on the layout without it
     # (every row one thread, same groups) and on Row-grouped CSR / Sliced
     # ELLPACK (groups of exactly 32 rows, one thread per row)
@@ -516,6 +554,7 @@ def run_ours(args):
             "baselines": baselines,
             "ablation": ablation,
             "d_sweep": d_sweep,
+            "families": families,
             "kernels": kernels,
         }
         print(json.dumps(line), flush=True)

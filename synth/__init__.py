@@ -425,6 +425,26 @@ def pathological_overflow_rowpointers(group_size: int = 128) -> tuple[np.ndarray
 # Named workloads (sizes as stated in the workload descriptions)
 # ---------------------------------------------------------------------------
 
+FAMILIES = ("banded_2m_hb8", "blockdiag_2m_b16", "zipf_300k")
+
+
+def family(name: str) -> Csr:
+    """The other matrix families of the SpMV report (values N(0, 1), FP64):
+
+    * ``banded_2m_hb8``: n = 2 000 000, full band |i - j| <= 8 (17 per row);
+    * ``blockdiag_2m_b16``: 125 000 dense 16 x 16 blocks on the diagonal;
+    * ``zipf_300k``: ``zipf_merged`` with n = 300 000, s = 1.5, rows of at
+      most 50 000 entries, generator seeded 3.
+    """
+    if name == "banded_2m_hb8":
+        return banded(2_000_000, 8)
+    if name == "blockdiag_2m_b16":
+        return block_diag(125_000, 16)
+    if name == "zipf_300k":
+        return zipf_merged(300_000, np.random.default_rng(3))
+    raise KeyError(name)
+
+
 def workload(name: str) -> tuple[Csr, np.ndarray]:
     """Return (A, x) for a named workload.
 

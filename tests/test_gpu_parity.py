@@ -136,6 +136,19 @@ def test_one_thread_per_row(G, D, V, storage):
         convert_and_check(A, G, D, V, storage=storage, one_thread_per_row=True)
 
 
+@pytest.mark.parametrize("family", ["banded", "blockdiag", "zipf"])
+@pytest.mark.parametrize("G,D", [(32, 1), (32, 4), (32, 17), (128, 4)])
+def test_matrix_families(family, G, D):
+    # the banded, block-structured and power-law families of the SpMV report
+    if family == "banded":
+        A = synth.banded(50_000, 8)
+    elif family == "blockdiag":
+        A = synth.block_diag(3000, 16)
+    else:
+        A = synth.zipf_merged(20_000, np.random.default_rng(3), max_len=5000)
+    convert_and_check(A, G, D, x_seed=4)
+
+
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
 @pytest.mark.parametrize("G,V", [(32, 1), (32, 4), (64, 2), (128, 1)])
 def test_random_low_precision_storage(storage, G, V):

@@ -92,6 +92,33 @@ def test_argument_checks_without_gpu(lib):
     assert lib.argcsr_baseline_csr_spmv(-3, 10, 0, 8, None, None, 0, 0, None, None, None) == api.ARGCSR_EINVAL
 
 
+def test_newer_calls_check_arguments_without_gpu(lib):
+    P = api.argcsr_params(32, 4, 1)
+    out = ctypes.c_void_p(123)
+    # unknown input or storage type, and a widening conversion
+    for in_dt, st_dt, status in ((5, 0, api.ARGCSR_EINVAL), (0, 9, api.ARGCSR_EINVAL),
+                                 (api.ARGCSR_F32, api.ARGCSR_F64, api.ARGCSR_ENOTSUP),
+                                 (api.ARGCSR_BF16, api.ARGCSR_F32, api.ARGCSR_ENOTSUP)):
+        assert lib.argcsr_create_from_csr_as(10, 10, 0, 8, None, None, in_dt, st_dt, ctypes.byref(P), None,
+                                             ctypes.byref(out)) == status
+        assert out.value is None
+    assert lib.argcsr_spmv_axpby(None, 1.0, None, 0.0, None, None) == api.ARGCSR_EINVAL
+    # an allocator needs both callbacks; none restores the pool
+    alloc = api.ALLOC_FN(lambda n, s, c: None)
+    assert lib.argcsr_set_allocator(ctypes.cast(alloc, ctypes.c_void_p), None, None) == api.ARGCSR_EINVAL
+    assert lib.argcsr_set_allocator(None, None, None) == api.ARGCSR_OK
+    # the serving calls refuse null handles and out-of-range parameters
+    assert lib.argcsr_server_add_matrix(None, None, None, None) == api.ARGCSR_EINVAL
+    assert lib.argcsr_server_query(None, 1, None) == api.ARGCSR_EINVAL
+    assert lib.argcsr_server_release(None, 1) == api.ARGCSR_EINVAL
+    assert lib.argcsr_server_destroy(None) == api.ARGCSR_OK
+    bad = api.argcsr_server_params(0, 0, 4, 17, 0, 0)      # max_batch above 16
+    h = ctypes.c_void_p()
+    assert lib.argcsr_server_create(ctypes.byref(bad), ctypes.byref(h)) == api.ARGCSR_EINVAL
+    bad = api.argcsr_server_params(0, 0, 4, 0, 0, 4)       # every slot kept for SpMV
+    assert lib.argcsr_server_create(ctypes.byref(bad), ctypes.byref(h)) == api.ARGCSR_EINVAL
+
+
 def test_python_errors_carry_the_status(lib):
     with pytest.raises(api.ArgcsrError) as e:
         api.argcsr_spmv(None, None, None)

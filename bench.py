@@ -73,8 +73,7 @@ def csr_spmv_bytes(n, n_cols, nnz):
 def kernel_bytes(kernel, n, n_cols, nnz, groups, slots):
     """Algorithmic bytes of one launch of each library kernel on one matrix."""
     return {
-        "k_next_delta": 4 * (n + 1) + n,
-        "k_tile_walk": n,
+        "k_tile_prepare": 4 * (n + 1) + n,          # rowPointers in, next-group deltas out
         "k_groups": 4 * (n + 1) + n + 4 * n + 16 * groups,
         "k_fill": nnz * (4 + SV) + 4 * (n + 1) + 4 * n + 16 * groups * 2 + slots * (4 + SV),
         "k_spmv_g32": spmv_bytes(n, n_cols, nnz, groups),

@@ -197,6 +197,7 @@ ARGCSR_API argcsr_status argcsr_destroy(argcsr_t A, argcsr_stream_t stream) {
     pool_free(A->d_threadsMapping, s);
     pool_free(A->d_columns, s);
     pool_free(A->d_values, s);
+    pool_free(A->d_longGroups, s);
     delete A;
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? ARGCSR_OK : record_cuda(e, "argcsr_destroy");

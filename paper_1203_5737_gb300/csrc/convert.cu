@@ -573,6 +573,24 @@ k_fill(long long nGroups, int n_cols, const long long *__restrict__ tileSlotBase
     if (__any_sync(FULL, bad) && lane == 0) flag(&tot->status, kBadColumn);
 }
 
+// ---------------------------------------------------------------------------
+// 7. The long groups (chunk size above kLongChunk) of a G = 32, V = 1 layout,
+//    listed for the SpMV, which gives each of them a whole block.  The list
+//    order is that of the atomic appends; every group is computed on its own,
+//    so it does not change any result.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_long_groups(long long nGroups, const int4 *__restrict__ gi, int *__restrict__ list, long long cap,
+              DeviceTotals *tot) {
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < nGroups;
+         g += (long long)gridDim.x * blockDim.x) {
+        if (__ldg(gi + g).w > kLongChunk) {
+            const long long i = atomicAdd(reinterpret_cast<unsigned long long *>(&tot->n_long), 1ull);
+            if (i < cap) list[i] = (int)g;
+        }
+    }
+}
+
 // Dynamic shared memory of k_groups: delta (T), starts (2T), chunk sizes
 // (4T), row lengths (4(T+G), padded), sub-tile tables (2 S G), sub-tile
 // entries and bases (4 S), threadsMapping of the tile's rows (4(T+G), padded).
@@ -781,12 +799,28 @@ extern "C" ARGCSR_API argcsr_status argcsr_create_from_csr_as(
 #undef FILL_G
 #undef FILL
     if (st != ARGCSR_OK) return fail(st);
+    // a long group holds more than kLongChunk * 32 slots
+    const long long longCap = G == 32 && V == 1 ? A->n_slots / ((long long)kLongChunk * 32) : 0;
+    if (longCap > 0) {
+        if ((st = pool_alloc((void **)&A->d_longGroups, (size_t)longCap * 4, s)) != ARGCSR_OK) return fail(st);
+        const unsigned blocks = (unsigned)min((long long)((A->n_groups + 255) / 256), 152LL * 8);
+        k_long_groups<<<blocks, 256, 0, s>>>(A->n_groups, A->d_groupInfo, A->d_longGroups, longCap, tot);
+        count_launches(1);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(record_cuda(e, "k_long_groups"));
+    }
     e = cudaMemcpyAsync(&h, tot, sizeof h, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(record_cuda(e, "conversion: read status"));
     if (h.status & kBadColumn) return fail(ARGCSR_EINVAL);
+    A->n_long = longCap > 0 ? (h.n_long < longCap ? h.n_long : longCap) : 0;
+    if (A->n_long == 0 && A->d_longGroups) {
+        pool_free(A->d_longGroups, s);
+        A->d_longGroups = nullptr;
+    }
 
-    A->device_bytes = (int64_t)A->n_groups * 16 + (int64_t)n * 4 + A->n_slots * (4 + (int64_t)es);
+    A->device_bytes = (int64_t)A->n_groups * 16 + (int64_t)n * 4 + A->n_slots * (4 + (int64_t)es) +
+                      (A->d_longGroups ? longCap * 4 : 0);
     *out = A;
     return ARGCSR_OK;
 }

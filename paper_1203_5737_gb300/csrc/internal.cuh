@@ -24,7 +24,13 @@ struct DeviceTotals {
     unsigned pad;
     long long n_groups;
     long long n_slots;
+    long long n_long;   // groups with more than kLongChunk slot rows
 };
+
+// A G = 32 group whose chunk size exceeds this is a "long group": its slot
+// rows are shared out among the 8 warps of a block (k_spmv_long_g32) rather
+// than walked by one warp.
+constexpr int kLongChunk = 64;
 
 }  // namespace argcsr
 
@@ -41,6 +47,8 @@ struct argcsr_matrix {
     int32_t *d_columns;         // S slots, -1 = padding
     void *d_values;             // S slots of dtype, +0.0 = padding
     int64_t device_bytes;
+    int32_t *d_longGroups = nullptr;   // indices of the long groups (G 32, V 1)
+    int64_t n_long = 0;
 };
 
 namespace argcsr {

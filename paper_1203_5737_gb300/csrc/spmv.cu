@@ -191,6 +191,46 @@ __device__ __forceinline__ void group_fixed(const int4 info, const int *__restri
 
 // G = 32: one warp per group.
 // y = A x, or y = b - A x when b is given (the residual of a solver).
+// A long group (G = 32, V = 1, chunk size above kLongChunk) on a whole
+// block (the first blocks of k_spmv_g32, so that they start at once and run
+// beside the other groups): warp w sums slot rows [w C / 8, (w + 1) C / 8) of every chunk (lane),
+// in element order; the 8 partial sums of a chunk are then added in warp
+// order, and the rows' chunks reduced as in k_spmv_g32.  The sums are split
+// in 8 where the one-warp loop keeps one, so the result can differ from it
+// in rounding (both stay within the summation bound the tests check).
+template <typename VT, typename AT, int MODE>
+__device__ __forceinline__ void long_group_block(const int4 info, const int *__restrict__ tm,
+                                                 const int *__restrict__ cols, const VT *__restrict__ vals,
+                                                 const AT *__restrict__ x, const Epi<AT> &ep,
+                                                 AT *__restrict__ y) {
+    __shared__ AT partial[8][32];
+    constexpr int U = ARGCSR_SPMV_ELEMS;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int C = info.w;
+    const int j0 = (int)((long long)C * warp / 8), j1 = (int)((long long)C * (warp + 1) / 8);
+    const long long base = (long long)info.z + lane + 32LL * j0;
+    const int *cp = cols + base;
+    const VT *vp = vals + base;
+    const int nb = j1 - j0;
+    AT sum = 0;
+    Batch<VT, 1, U> B;
+    load_batch<VT, 1, U>(B, cp, vp, 32LL, 0, nb, true);
+    for (int b = 0; b < nb; b += U) {
+        Batch<VT, 1, U> N;
+        load_batch<VT, 1, U>(N, cp, vp, 32LL, b + U, nb, true);
+        consume<VT, AT, 1, U>(B, x, sum);
+        B = N;
+    }
+    partial[warp][lane] = sum;
+    __syncthreads();
+    if (warp != 0) return;
+    AT s = partial[0][lane];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) s += partial[w][lane];
+    const RowEnds m(tm, info.x, info.y, lane);
+    reduce_store<MODE, AT>(m.owns ? s : AT(0), m, info.x, lane, ep, y);
+}
+
 // Register budgets: 32 with FP32 accumulation, so that 64 warps fit on an
 // SM (the gathers need every warp in flight), 40 with FP64 (48 warps; 51 for
 // V = 4, whose wider loads need more).
@@ -198,11 +238,17 @@ template <typename VT, typename AT, int V, int MODE>
 __global__ void __launch_bounds__(256, sizeof(AT) == 4 ? 8 : (V == 4 ? 5 : 6))
 k_spmv_g32(long long nGroups, const int4 *__restrict__ gi, const int *__restrict__ tm,
            const int *__restrict__ cols, const VT *__restrict__ vals, const AT *__restrict__ x,
-           const Epi<AT> ep, AT *__restrict__ y) {
+           const Epi<AT> ep, AT *__restrict__ y, const int *__restrict__ longList, int nLong) {
     using Acc = AT;
     constexpr int U = (ARGCSR_SPMV_ELEMS + V - 1) / V;
     const int lane = threadIdx.x & 31;
-    const long long g = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if constexpr (V == 1) {
+        if ((int)blockIdx.x < nLong) {   // block-uniform: the long groups first
+            long_group_block<VT, AT, MODE>(__ldg(gi + __ldg(longList + blockIdx.x)), tm, cols, vals, x, ep, y);
+            return;
+        }
+    }
+    const long long g = (long long)(blockIdx.x - nLong) * 8 + (threadIdx.x >> 5);
     if (g >= nGroups) return;  // warp-uniform
     const int4 info = __ldg(gi + g);  // firstRow, size, offset, chunkSize
     const int first = info.x, size = info.y, C = info.w;
@@ -221,6 +267,7 @@ k_spmv_g32(long long nGroups, const int4 *__restrict__ gi, const int *__restrict
         }
     }
 #endif
+    if (nLong > 0 && C > kLongChunk) return;   // done by one of the first blocks (warp-uniform)
     const long long base = (long long)info.z + lane * V;
     // the first batch does not depend on threadsMapping: issue it together
     Batch<VT, V, U> B;
@@ -281,8 +328,12 @@ argcsr_status launch_typed(const argcsr_matrix *A, const void *x, const Epi<AT> 
     static const char *names[2][3] = {{"k_spmv_g32", "k_residual_g32", "k_spmv_axpby_g32"},
                                       {"k_spmv_block", "k_residual_block", "k_spmv_axpby_block"}};
     TraceScope t(names[A->G == 32 ? 0 : 1][MODE], s);
+    const int nLong = V == 1 && A->G == 32 ? (int)A->n_long : 0;
     switch (A->G) {
-        case 32: k_spmv_g32<VT, AT, V, MODE><<<(unsigned)((ng + 7) / 8), 256, 0, s>>>(ng, gi, tm, cols, vals, xx, ep, yy); break;
+        case 32:
+            k_spmv_g32<VT, AT, V, MODE><<<(unsigned)((ng + 7) / 8 + nLong), 256, 0, s>>>(
+                ng, gi, tm, cols, vals, xx, ep, yy, A->d_longGroups, nLong);
+            break;
         case 64: k_spmv_block<64, VT, AT, V, MODE><<<(unsigned)((ng + 3) / 4), 256, 0, s>>>(ng, gi, tm, cols, vals, xx, ep, yy); break;
         default: k_spmv_block<128, VT, AT, V, MODE><<<(unsigned)((ng + 1) / 2), 256, 0, s>>>(ng, gi, tm, cols, vals, xx, ep, yy); break;
     }

@@ -19,7 +19,7 @@ def test_byte_model_by_hand():
 
 
 def test_kernel_bytes_cover_the_traced_kernels():
-    for k in ("k_next_delta", "k_tile_walk", "k_groups", "k_fill", "k_spmv_g32", "k_spmv_block"):
+    for k in ("k_tile_prepare", "k_groups", "k_fill", "k_spmv_g32", "k_spmv_block"):
         assert bench.kernel_bytes(k, 10, 10, 30, 2, 64) > 0
     assert bench.kernel_bytes("k_spmv_g32", 10, 10, 30, 2, 64) == bench.spmv_bytes(10, 10, 30, 2)
 

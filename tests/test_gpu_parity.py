@@ -136,6 +136,46 @@ def test_one_thread_per_row(G, D, V, storage):
         convert_and_check(A, G, D, V, storage=storage, one_thread_per_row=True)
 
 
+@pytest.mark.parametrize("storage", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("D", [1, 4])
+def test_long_groups_split_over_a_block(storage, D):
+    # rows of 2 000 - 40 000 entries: groups of chunk size above 64, whose slot
+    # rows the SpMV shares out among the 8 warps of a block; the product,
+    # the residual and y = alpha A x + beta y all go through that path
+    rng = np.random.default_rng(40 + D)
+    n, n_cols = 20_000, 45_000
+    lens = rng.geometric(1 / 7, n) - 1
+    lens[rng.choice(n, 12, replace=False)] = rng.integers(2_000, 40_000, 12)
+    rp = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(lens, out=rp[1:])
+    row = np.repeat(np.arange(n), lens)
+    k = np.arange(int(rp[-1])) - np.repeat(rp[:-1], lens)
+    cols = np.where(np.repeat(lens, lens) > 100, (row * 7919) % (n_cols - 40_000) + k,
+                    (row * 31 + k * 977) % n_cols)       # distinct within each row
+    A = synth.Csr(n, n_cols, rp.astype(np.int32), cols.astype(np.int32),
+                  rng.standard_normal(int(rp[-1])), "long_rows")
+    ref = convert_and_check(A, 32, D, storage=storage, x_seed=6)
+    assert np.sum(ref.groupInfo[:, 3] > 64) >= 10      # the split path is taken
+    rpd, cd, vd, As = to_device(A, storage)
+    vdt = np.float64 if storage == "f64" else np.float32
+    x = synth.uniform_vector(n_cols, 7, vdt)
+    y0 = synth.uniform_vector(n, 8, vdt)
+    with ArgCsrMatrix.from_csr(rpd, cd, vd, n_cols, group_size=32, desired_chunk_size=D) as M:
+        y = torch.from_numpy(y0.copy()).to(DEV)
+        M.spmv_axpby(torch.from_numpy(x).to(DEV), y, -1.5, 0.5)
+        b = torch.from_numpy(synth.uniform_vector(n, 9)).to(DEV)
+        r = M.residual(b, torch.from_numpy(x.astype(np.float64)).to(DEV)) if n == n_cols else None
+        torch.cuda.synchronize()
+        got = y.cpu().numpy().astype(np.float64)
+    ax = oracle.csr_spmv(As, x.astype(np.float64))
+    scale = oracle.csr_abs_spmv(As, x.astype(np.float64))
+    lens_s = As.row_lengths()
+    tol = (1.5 * (1e-13 if storage == "f64" else 2.0 * (lens_s + 2) * 2.0 ** -24) * scale
+           + 4 * 2.0 ** (-53 if storage == "f64" else -24) * (np.abs(1.5 * ax) + np.abs(0.5 * y0)))
+    assert np.all(np.abs(got - (-1.5 * ax + 0.5 * y0.astype(np.float64))) <= tol)
+    del r
+
+
 @pytest.mark.parametrize("family", ["banded", "blockdiag", "zipf"])
 @pytest.mark.parametrize("G,D", [(32, 1), (32, 4), (32, 17), (128, 4)])
 def test_matrix_families(family, G, D):

@@ -40,6 +40,8 @@ def _pool():
         (synth.laplacian_3d(14, 12, 10), "f32", 64, True),
         (synth.lognormal_rows(4000, mu=1.8, sigma=1.0, max_len=500, seed_structure=3), "f32", 32, False),
         (synth.random_csr(2000, 1500, 4, mean_len=6, n_huge=2, huge_len=1200), "f64", 128, False),
+        # rows of 2900 entries: long groups, which the SpMV splits over a block
+        (synth.random_csr(3000, 3000, 9, mean_len=5, n_huge=3, huge_len=2900), "f32", 32, False),
     ]
 
 

@@ -215,12 +215,8 @@ struct argcsr_server {
                 if (!head) break;
                 const Matrix &m = mats[head->matrix];
                 if (head->type == 0) {
-                    // the head and later SpMV requests on the same matrix; a
-                    // matrix with long groups is not fused (its SpMV splits
-                    // them over a block, the SpMM does not, and a request
-                    // must give the same result alone and in the mix)
-                    const int cap = m.A->n_long > 0 ? 1 : P.max_batch;
-                    for (auto it = pending.begin(); it != pending.end() && (int)take.size() < cap; ++it)
+                    // the head and later SpMV requests on the same matrix
+                    for (auto it = pending.begin(); it != pending.end() && (int)take.size() < P.max_batch; ++it)
                         if ((*it)->type == 0 && (*it)->matrix == head->matrix) take.push_back(*it);
                     while (!take.empty() && spmv_bytes(m, (int)take.size()) > budget_left()) take.pop_back();
                     if (take.empty()) take.push_back(head);   // k = 1 needs no memory

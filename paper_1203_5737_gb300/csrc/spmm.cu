@@ -120,14 +120,77 @@ __device__ __forceinline__ void spmm_group_g32(const int4 info, const int *__res
     if (rm.owns && lane == rm.segStart) store_y_row<AT, K, VEC>(Y + (long long)(first + rm.row) * ldy, acc);
 }
 
+// A long group (V = 1, chunk size above kLongChunk) on a whole block, as the
+// SpMV does it: warp w takes slot rows [w C / 8, (w + 1) C / 8) of every
+// chunk, the 8 partial sums are added in warp order, then the rows are
+// reduced.  Every column's arithmetic is the SpMV's, so column j of Y equals
+// the SpMV of column j of X bit for bit here too.
+template <typename VT, typename AT, int K, bool VEC>
+__device__ __forceinline__ void spmm_long_block(const int4 info, const int *__restrict__ tm,
+                                                const int *__restrict__ cols, const VT *__restrict__ vals,
+                                                const AT *__restrict__ X, long long ldx,
+                                                AT *__restrict__ Y, long long ldy) {
+    __shared__ AT partial[8][32][K];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int C = info.w;
+    const int j0 = (int)((long long)C * warp / 8), j1 = (int)((long long)C * (warp + 1) / 8);
+    const long long base = (long long)info.z + lane;
+    AT acc[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) acc[q] = 0;
+#pragma unroll 2
+    for (int j = j0; j < j1; ++j) {
+        int c[1];
+        VT v[1];
+        ld_stream<int, 1>(cols + base + 32LL * j, c);
+        ld_stream<VT, 1>(vals + base + 32LL * j, v);
+        if (c[0] >= 0) {
+            AT xv[K];
+            load_x_row<AT, K, VEC>(X + (long long)c[0] * ldx, xv);
+            const AT a = (AT)widen(v[0]);
+#pragma unroll
+            for (int q = 0; q < K; ++q) acc[q] = fma(a, xv[q], acc[q]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < K; ++q) partial[warp][lane][q] = acc[q];
+    __syncthreads();
+    if (warp != 0) return;
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        acc[q] = partial[0][lane][q];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) acc[q] += partial[w][lane][q];
+    }
+    const WarpRowMap rm(tm, info.x, info.y, lane);
+    const int maxChunks = __reduce_max_sync(FULL, rm.owns ? rm.segEnd - rm.segStart : 0);
+    for (int o = 1; o < maxChunks; o <<= 1) {
+        const bool on = ((lane - rm.segStart) & (2 * o - 1)) == 0 && lane + o < rm.segEnd;
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            const AT t = __shfl_down_sync(FULL, acc[q], o);
+            add_if(acc[q], t, on);
+        }
+    }
+    if (rm.owns && lane == rm.segStart) store_y_row<AT, K, VEC>(Y + (long long)(info.x + rm.row) * ldy, acc);
+}
+
 template <typename VT, typename AT, int K, int V, bool VEC>
 __global__ void __launch_bounds__(256)
 k_spmm_g32(long long nGroups, const int4 *__restrict__ gi, const int *__restrict__ tm,
            const int *__restrict__ cols, const VT *__restrict__ vals, const AT *__restrict__ X,
-           long long ldx, AT *__restrict__ Y, long long ldy) {
-    const long long g = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+           long long ldx, AT *__restrict__ Y, long long ldy, const int *__restrict__ longList, int nLong) {
+    if constexpr (V == 1) {
+        if ((int)blockIdx.x < nLong) {   // block-uniform: the long groups first
+            spmm_long_block<VT, AT, K, VEC>(__ldg(gi + __ldg(longList + blockIdx.x)), tm, cols, vals, X, ldx, Y, ldy);
+            return;
+        }
+    }
+    const long long g = (long long)(blockIdx.x - nLong) * 8 + (threadIdx.x >> 5);
     if (g >= nGroups) return;
-    spmm_group_g32<VT, AT, K, V, VEC>(__ldg(gi + g), tm, cols, vals, X, ldx, Y, ldy, threadIdx.x & 31);
+    const int4 info = __ldg(gi + g);
+    if (nLong > 0 && info.w > kLongChunk) return;   // done by one of the first blocks (warp-uniform)
+    spmm_group_g32<VT, AT, K, V, VEC>(info, tm, cols, vals, X, ldx, Y, ldy, threadIdx.x & 31);
 }
 
 // G = 64 / 128: one group per G threads, the row owner adds its chunks.
@@ -359,7 +422,12 @@ void launch_spmm_kvv(const argcsr_matrix *A, const void *X, long long ldx, void 
     const auto *xx = static_cast<const AT *>(X);
     auto *yy = static_cast<AT *>(Y);
     switch (A->G) {
-        case 32: k_spmm_g32<VT, AT, K, V, VEC><<<(unsigned)((ng + 7) / 8), 256, 0, s>>>(ng, A->d_groupInfo, A->d_threadsMapping, A->d_columns, vals, xx, ldx, yy, ldy); break;
+        case 32: {
+            const int nLong = V == 1 ? (int)A->n_long : 0;
+            k_spmm_g32<VT, AT, K, V, VEC><<<(unsigned)((ng + 7) / 8 + nLong), 256, 0, s>>>(
+                ng, A->d_groupInfo, A->d_threadsMapping, A->d_columns, vals, xx, ldx, yy, ldy, A->d_longGroups, nLong);
+            break;
+        }
         case 64: k_spmm_block<64, VT, AT, K, V, VEC><<<(unsigned)((ng + 3) / 4), 256, 0, s>>>(ng, A->d_groupInfo, A->d_threadsMapping, A->d_columns, vals, xx, ldx, yy, ldy); break;
         default: k_spmm_block<128, VT, AT, K, V, VEC><<<(unsigned)((ng + 1) / 2), 256, 0, s>>>(ng, A->d_groupInfo, A->d_threadsMapping, A->d_columns, vals, xx, ldx, yy, ldy); break;
     }

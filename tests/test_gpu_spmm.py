@@ -70,6 +70,27 @@ def test_spmm_matches_columnwise_oracle(k, storage, G, V):
     assert torch.equal(Y, Y2)
 
 
+@pytest.mark.parametrize("k", [1, 2, 8, 16])
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_spmm_long_groups_equal_spmv_bitwise(k, storage):
+    # rows of thousands of entries: the product splits their groups over a
+    # block; every column of Y must equal the SpMV of that column bit for bit
+    A = synth.random_csr(6000, 9000, 17, mean_len=5, n_huge=6, huge_len=8000)
+    vd, As = stored(A, storage)
+    vdt = np.float64 if storage == "f64" else np.float32
+    X = np.random.default_rng(k).uniform(-1, 1, (A.n_cols, k)).astype(vdt)
+    rp = torch.from_numpy(A.rowPointers).to(DEV)
+    cols = torch.from_numpy(A.columns).to(DEV)
+    with ArgCsrMatrix.from_csr(rp, cols, vd, A.n_cols, group_size=32, desired_chunk_size=2) as M:
+        Xd = torch.from_numpy(X).to(DEV)
+        Y = M.spmm(Xd)
+        ys = [M.spmv(Xd[:, j].contiguous()) for j in range(k)]
+        torch.cuda.synchronize()
+    for j in range(k):
+        assert torch.equal(Y[:, j], ys[j]), f"column {j}"
+    check_cols(Y.cpu().numpy(), As, X, storage)
+
+
 def _batch_matrices(count, seed, storage):
     rng = np.random.default_rng(seed)
     mats = []

@@ -482,24 +482,113 @@ __device__ __forceinline__ VO to_storage(VI v) {
     }
 }
 
+// One chunk of a group: C elements from src (fill of them real, the rest
+// padding) to slots out[(j / V) G V + j % V], j < C.
+template <int G, int V, typename VT, typename VO>
+__device__ __forceinline__ void copy_chunk(const int *__restrict__ cIn, const VT *__restrict__ vIn, int fill,
+                                           int C, int n_cols, int *__restrict__ cOut, VO *__restrict__ vOut,
+                                           bool &bad) {
+    for (int j0 = 0; j0 < C; j0 += 4) {
+        int cc[4];
+        VT vv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = j0 + u;
+            cc[u] = -1;
+            memset(&vv[u], 0, sizeof(VT));
+            if (j < fill) {
+                cc[u] = cIn[j];
+                vv[u] = vIn[j];
+                bad |= (cc[u] < 0) | (cc[u] >= n_cols);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = j0 + u;
+            if (j < C) {
+                const int at = (j / V) * (G * V) + (j % V);
+                cOut[at] = cc[u];
+                vOut[at] = to_storage<VO>(vv[u]);
+            }
+        }
+    }
+}
+
+// G = 32: one warp per group.  A group's loads form two dependent rounds:
+// its slot base, threadsMapping words and row pointers (lane l reads those
+// of row l; the bounds of the row a chunk belongs to come by shuffle), then
+// its entries.  The record of the warp's next group is loaded one group
+// ahead.
+template <typename VT, typename VO, int V>
+__device__ __forceinline__ void fill_g32(long long nGroups, int n_cols, const long long *__restrict__ tileSlotBase,
+                                         const int4 *__restrict__ gscratch, const int *__restrict__ rp,
+                                         const int *__restrict__ colsIn, const VT *__restrict__ valsIn,
+                                         const int *__restrict__ threadsMapping, int4 *__restrict__ groupInfo,
+                                         int *__restrict__ colsOut, VO *__restrict__ valsOut,
+                                         int *__restrict__ longList, long long longCap, DeviceTotals *tot) {
+    const int lane = threadIdx.x & 31;
+    const long long W = (long long)gridDim.x * (blockDim.x >> 5);
+    long long g = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    bool bad = false;
+    int4 next = g < nGroups ? gscratch[g] : make_int4(0, 0, 0, 0);
+    for (; g < nGroups; g += W) {
+        const int4 s = next;
+        if (g + W < nGroups) next = gscratch[g + W];
+        const int first = s.x, size = s.y & 255, C = s.w;
+        const int off = (int)(tileSlotBase[s.y >> 8] + s.z);
+        const int end = lane < size ? threadsMapping[first + lane] : 0;
+        const int rowStart = lane < size ? rp[first + lane] : 0;
+        const int lastEnd = rp[first + size];
+        if (lane == 0) {
+            groupInfo[g] = make_int4(first, size, off, C);
+            if (longList && C > kLongChunk) {
+                const long long i = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&tot->n_long), 1ull);
+                if (i < longCap) longList[i] = (int)g;
+            }
+        }
+        if (C <= 0) continue;   // warp-uniform
+        // row ends as a bit mask: the row of chunk `lane` is the number of
+        // ends below it, its first chunk follows the previous end
+        const unsigned ends = __reduce_or_sync(FULL, lane < size ? 1u << (end - 1) : 0u);
+        const unsigned below = ends & ((1u << lane) - 1u);
+        const int row = __popc(below), begin = below ? 32 - __clz(below) : 0;
+        const int rs = __shfl_sync(FULL, rowStart, min(row, 31));
+        const int reNext = __shfl_sync(FULL, rowStart, min(row + 1, 31));
+        int src = 0, fill = 0;
+        if (row < size) {
+            const int re = row + 1 < size ? reNext : lastEnd;
+            src = rs + (lane - begin) * C;
+            fill = max(0, min(C, re - src));
+        }
+        copy_chunk<32, V>(colsIn + src, valsIn + src, fill, C, n_cols, colsOut + off + lane * V,
+                          valsOut + off + lane * V, bad);
+    }
+    if (__any_sync(FULL, bad) && lane == 0) flag(&tot->status, kBadColumn);
+}
+
 template <int G, typename VT, typename VO, int V>
 __global__ void __launch_bounds__(256)
 k_fill(long long nGroups, int n_cols, const long long *__restrict__ tileSlotBase,
        const int4 *__restrict__ gscratch, const int *__restrict__ rp, const int *__restrict__ colsIn,
        const VT *__restrict__ valsIn, const int *__restrict__ threadsMapping,
        int4 *__restrict__ groupInfo, int *__restrict__ colsOut, VO *__restrict__ valsOut,
-       DeviceTotals *tot) {
-    __shared__ short s_rowOf[8][G];     // chunk -> row of the group (G > 32)
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-    bool bad = false;
-    for (long long g = (long long)blockIdx.x * (blockDim.x >> 5) + warp; g < nGroups; g += warps) {
-        const int4 s = gscratch[g];
-        const int first = s.x, size = s.y & 255, C = s.w;
-        const long long off = tileSlotBase[s.y >> 8] + s.z;
-        if (lane == 0) groupInfo[g] = make_int4(first, size, (int)off, C);
-        if (C <= 0) continue;
-        if constexpr (G > 32) {
+       int *__restrict__ longList, long long longCap, DeviceTotals *tot) {
+    if constexpr (G == 32) {
+        fill_g32<VT, VO, V>(nGroups, n_cols, tileSlotBase, gscratch, rp, colsIn, valsIn, threadsMapping,
+                            groupInfo, colsOut, valsOut, longList, longCap, tot);
+    } else {
+        // G = 64 or 128: one group per warp; the row of each chunk from a
+        // per-warp table built from threadsMapping
+        __shared__ short s_rowOf[8][G];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+        bool bad = false;
+        for (long long g = (long long)blockIdx.x * (blockDim.x >> 5) + warp; g < nGroups; g += warps) {
+            const int4 s = gscratch[g];
+            const int first = s.x, size = s.y & 255, C = s.w;
+            const long long off = tileSlotBase[s.y >> 8] + s.z;
+            if (lane == 0) groupInfo[g] = make_int4(first, size, (int)off, C);
+            if (C <= 0) continue;
             for (int c = lane; c < G; c += 32) s_rowOf[warp][c] = -1;
             __syncwarp();
             for (int r = lane; r < size; r += 32) {
@@ -507,87 +596,27 @@ k_fill(long long nGroups, int n_cols, const long long *__restrict__ tileSlotBase
                 for (int c = b; c < e; ++c) s_rowOf[warp][c] = (short)r;
             }
             __syncwarp();
-        }
 #pragma unroll
-        for (int q = 0; q < G / 32; ++q) {
-            const int c = q * 32 + lane;
-            int row, begin;
-            if constexpr (G == 32) {
-                // row ends as a bit mask: the row of chunk c is the number of
-                // ends below c, its first chunk follows the previous end
-                const int end = lane < size ? threadsMapping[first + lane] : 0;
-                const unsigned ends = __reduce_or_sync(FULL, lane < size ? 1u << (end - 1) : 0u);
-                const unsigned below = ends & ((1u << lane) - 1u);
-                row = __popc(below);
-                begin = below ? 32 - __clz(below) : 0;
-            } else {
-                row = s_rowOf[warp][c];
+            for (int q = 0; q < G / 32; ++q) {
+                const int c = q * 32 + lane;
+                int row = s_rowOf[warp][c];
                 if (row < 0) row = size;
-                begin = (row > 0 && row < size) ? threadsMapping[first + row - 1] : 0;
-            }
-            long long src = 0;
-            int fill = 0;
-            if (row < size) {
-                const int r = first + row;
-                const int rs = rp[r];
-                const long long kk = (long long)(c - begin) * C;
-                const long long len = (long long)rp[r + 1] - rs;
-                src = rs + kk;
-                fill = (int)min((long long)C, max(0LL, len - kk));
-            }
-            // a chunk's elements are contiguous in the CSR arrays; lanes of one
-            // row read C apart, which L1 serves from the lines already fetched.
-            // Element j of chunk c goes to off + (j/V)*G*V + c*V + j%V; the
-            // part that depends on j stays below C*G < 2^31.
-            const int *cIn = colsIn + src;
-            const VT *vIn = valsIn + src;
-            int *cOut = colsOut + off + (long long)c * V;
-            VO *vOut = valsOut + off + (long long)c * V;
-            for (int j0 = 0; j0 < C; j0 += 4) {
-                int cc[4];
-                VT vv[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int j = j0 + u;
-                    cc[u] = -1;
-                    memset(&vv[u], 0, sizeof(VT));
-                    if (j < fill) {
-                        cc[u] = cIn[j];
-                        vv[u] = vIn[j];
-                        bad |= (cc[u] < 0) | (cc[u] >= n_cols);
-                    }
+                const int begin = (row > 0 && row < size) ? threadsMapping[first + row - 1] : 0;
+                int src = 0, fill = 0;
+                if (row < size) {
+                    const int rs = rp[first + row], re = rp[first + row + 1];
+                    src = rs + (c - begin) * C;
+                    fill = max(0, min(C, re - src));
                 }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int j = j0 + u;
-                    if (j < C) {
-                        const int at = (j / V) * (G * V) + (j % V);
-                        cOut[at] = cc[u];
-                        vOut[at] = to_storage<VO>(vv[u]);
-                    }
-                }
+                // a chunk's elements are contiguous in the CSR arrays; lanes of
+                // one row read C apart, which L1 serves from the lines already
+                // fetched
+                copy_chunk<G, V>(colsIn + src, valsIn + src, fill, C, n_cols, colsOut + off + c * V,
+                                 valsOut + off + c * V, bad);
             }
+            __syncwarp();
         }
-        if constexpr (G > 32) __syncwarp();
-    }
-    if (__any_sync(FULL, bad) && lane == 0) flag(&tot->status, kBadColumn);
-}
-
-// ---------------------------------------------------------------------------
-// 7. The long groups (chunk size above kLongChunk) of a G = 32, V = 1 layout,
-//    listed for the SpMV, which gives each of them a whole block.  The list
-//    order is that of the atomic appends; every group is computed on its own,
-//    so it does not change any result.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256)
-k_long_groups(long long nGroups, const int4 *__restrict__ gi, int *__restrict__ list, long long cap,
-              DeviceTotals *tot) {
-    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < nGroups;
-         g += (long long)gridDim.x * blockDim.x) {
-        if (__ldg(gi + g).w > kLongChunk) {
-            const long long i = atomicAdd(reinterpret_cast<unsigned long long *>(&tot->n_long), 1ull);
-            if (i < cap) list[i] = (int)g;
-        }
+        if (__any_sync(FULL, bad) && lane == 0) flag(&tot->status, kBadColumn);
     }
 }
 
@@ -642,7 +671,8 @@ struct Kernels {
                                   const long long *tileSlotBase,
                                   const int4 *gscratch, const int *rp, const int *cols,
                                   const void *vals, const int *tm, int4 *gi, int *colsOut,
-                                  void *valsOut, DeviceTotals *tot, cudaStream_t s) {
+                                  void *valsOut, int *longList, long long longCap, DeviceTotals *tot,
+                                  cudaStream_t s) {
         if (nGroups == 0) return ARGCSR_OK;
         const long long blocks = min((nGroups + 7) / 8, 152LL * 64);
         TraceScope t("k_fill", s);
@@ -650,13 +680,16 @@ struct Kernels {
         VO *vo = static_cast<VO *>(valsOut);
         if (V == 1)
             k_fill<G, VT, VO, 1><<<(unsigned)blocks, 256, 0, s>>>(nGroups, n_cols, tileSlotBase, gscratch, rp,
-                                                                  cols, v, tm, gi, colsOut, vo, tot);
+                                                                  cols, v, tm, gi, colsOut, vo, longList,
+                                                                  longCap, tot);
         else if (V == 2)
             k_fill<G, VT, VO, 2><<<(unsigned)blocks, 256, 0, s>>>(nGroups, n_cols, tileSlotBase, gscratch, rp,
-                                                                  cols, v, tm, gi, colsOut, vo, tot);
+                                                                  cols, v, tm, gi, colsOut, vo, nullptr, 0,
+                                                                  tot);
         else
             k_fill<G, VT, VO, 4><<<(unsigned)blocks, 256, 0, s>>>(nGroups, n_cols, tileSlotBase, gscratch, rp,
-                                                                  cols, v, tm, gi, colsOut, vo, tot);
+                                                                  cols, v, tm, gi, colsOut, vo, nullptr, 0,
+                                                                  tot);
         count_launches(1);
         ARGCSR_CHECK_LAUNCH("k_fill");
         return ARGCSR_OK;
@@ -780,12 +813,18 @@ extern "C" ARGCSR_API argcsr_status argcsr_create_from_csr_as(
     if ((st = pool_alloc((void **)&A->d_groupInfo, (size_t)A->n_groups * 16, s)) != ARGCSR_OK) return fail(st);
     if ((st = pool_alloc((void **)&A->d_columns, (size_t)A->n_slots * 4, s)) != ARGCSR_OK) return fail(st);
     if ((st = pool_alloc(&A->d_values, (size_t)A->n_slots * es, s)) != ARGCSR_OK) return fail(st);
+    // k_fill lists the long groups (G = 32, V = 1) for the SpMV; a long
+    // group holds more than kLongChunk * 32 slots
+    const long long longCap = G == 32 && V == 1 ? A->n_slots / ((long long)kLongChunk * 32) : 0;
+    if (longCap > 0 &&
+        (st = pool_alloc((void **)&A->d_longGroups, (size_t)longCap * 4, s)) != ARGCSR_OK)
+        return fail(st);
 
 #define FILL(GG, VI, VO)                                                                         \
     Kernels<GG>::template run_fill<VI, VO>(A->n_groups, V, n_cols, tileSlotBase,                   \
                                            gscratch, d_rowPointers, d_columns, d_values,          \
                                            A->d_threadsMapping, A->d_groupInfo, A->d_columns,     \
-                                           A->d_values, tot, s)
+                                           A->d_values, A->d_longGroups, longCap, tot, s)
 #define FILL_G(VI, VO) (G == 32 ? FILL(32, VI, VO) : G == 64 ? FILL(64, VI, VO) : FILL(128, VI, VO))
     if (in_dtype == dtype) {
         if (es == 8) st = FILL_G(double, double);
@@ -799,16 +838,6 @@ extern "C" ARGCSR_API argcsr_status argcsr_create_from_csr_as(
 #undef FILL_G
 #undef FILL
     if (st != ARGCSR_OK) return fail(st);
-    // a long group holds more than kLongChunk * 32 slots
-    const long long longCap = G == 32 && V == 1 ? A->n_slots / ((long long)kLongChunk * 32) : 0;
-    if (longCap > 0) {
-        if ((st = pool_alloc((void **)&A->d_longGroups, (size_t)longCap * 4, s)) != ARGCSR_OK) return fail(st);
-        const unsigned blocks = (unsigned)min((long long)((A->n_groups + 255) / 256), 152LL * 8);
-        k_long_groups<<<blocks, 256, 0, s>>>(A->n_groups, A->d_groupInfo, A->d_longGroups, longCap, tot);
-        count_launches(1);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return fail(record_cuda(e, "k_long_groups"));
-    }
     e = cudaMemcpyAsync(&h, tot, sizeof h, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(record_cuda(e, "conversion: read status"));
@@ -945,7 +974,8 @@ extern "C" ARGCSR_API argcsr_status argcsr_convert_noalloc(
 #define FILL(GG, VT)                                                                              \
     Kernels<GG>::template run_fill<VT>(h.n_groups, V, n_cols, tileSlotBase,                        \
                                        gscratch, d_rowPointers, d_columns, d_values,               \
-                                       d_threadsMapping, gi, d_out_columns, d_out_values, tot, s)
+                                       d_threadsMapping, gi, d_out_columns, d_out_values, nullptr, 0, \
+                                       tot, s)
     if (es == 8) st = G == 32 ? FILL(32, double) : G == 64 ? FILL(64, double) : FILL(128, double);
     else if (es == 4) st = G == 32 ? FILL(32, float) : G == 64 ? FILL(64, float) : FILL(128, float);
     else st = G == 32 ? FILL(32, uint16_t) : G == 64 ? FILL(64, uint16_t) : FILL(128, uint16_t);

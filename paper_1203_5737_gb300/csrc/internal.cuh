@@ -28,8 +28,8 @@ struct DeviceTotals {
 };
 
 // A G = 32 group whose chunk size exceeds this is a "long group": its slot
-// rows are shared out among the 8 warps of a block (k_spmv_long_g32) rather
-// than walked by one warp.
+// rows are shared out among the 8 warps of one of the first blocks of the
+// product kernels rather than walked by one warp.  k_fill lists them.
 constexpr int kLongChunk = 64;
 
 }  // namespace argcsr

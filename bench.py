@@ -313,11 +313,21 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    # kernel shares from a traced pass of the same steps before the timed
+    # region: an event pair around every launch adds about 50 us to a step,
+    # so the timed region traces only the dominant kernel
+    api.argcsr_trace_begin()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    api.argcsr_trace_end()
+    shares = api.trace_summary()
+    dominant = max(shares, key=lambda k: shares[k][1])
     barrier(world)
     launches0 = api.argcsr_launch_count()
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
-    api.argcsr_trace_begin()
+    api.argcsr_trace_begin_kernel(dominant)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
@@ -334,9 +344,9 @@ def run_ours(args):
     value = total_bytes / (ms_max * 1e-3) / 1e9
     trace = api.trace_summary()
 
-    # roofline of the dominant kernel (largest share of traced time)
+    # roofline of the dominant kernel (largest share of the traced pass),
+    # timed by its own events inside the timed region
     peak, peak_kind = measured_hbm_peak()
-    dominant = max(trace, key=lambda k: trace[k][1])
     launches_k, ms_k = trace[dominant]
     per_step = sum(kernel_bytes(dominant, m.n, m.n_cols, m.nnz, m.groups, m.slots) for m in mats)
     kbytes = per_step * args.steps
@@ -348,9 +358,9 @@ def run_ours(args):
                 "bytes_per_launch": round(kbytes / launches_k),
                 "avg_launch_us": round(ms_k * 1e3 / launches_k, 2),
                 "other_limits_ncu": ncu_limits(dominant)}
-    total_traced = sum(v[1] for v in trace.values())
+    total_traced = sum(v[1] for v in shares.values())
     kernels = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / total_traced, 4)}
-               for k, v in sorted(trace.items(), key=lambda kv: -kv[1][1])}
+               for k, v in sorted(shares.items(), key=lambda kv: -kv[1][1])}
 
     # SpMV alone (the paper's measured operation), baselines on the same GPU
     spmv = {}
@@ -555,6 +565,8 @@ def run_ours(args):
             "d_sweep": d_sweep,
             "families": families,
             "kernels": kernels,
+            "kernels_pass": "a traced pass of the same steps before the timed region, "
+                            "which traces only the dominant kernel",
         }
         print(json.dumps(line), flush=True)
     if world > 1:

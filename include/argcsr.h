@@ -509,11 +509,20 @@ ARGCSR_API argcsr_status argcsr_trim_pool(void);
  * Kernel tracing, a profiling aid (off by default).  Between
  * argcsr_trace_begin and argcsr_trace_end the library records a CUDA event
  * pair around every kernel it launches, on the stream it launches on.
+ * argcsr_trace_begin creates the events of the first 2048 launches up front
+ * (on the current device), so that they are not created inside the traced
+ * region.
  * argcsr_trace_end waits for the recorded events and sums the durations per
  * kernel; argcsr_trace_kernel then reads, for kernel index 0 .. count-1, its
  * name (static storage), number of launches and total milliseconds.
  * ------------------------------------------------------------------------ */
 ARGCSR_API argcsr_status argcsr_trace_begin(void);
+/* As argcsr_trace_begin, but events are recorded only around launches of
+ * the kernel named `name` (for instance "k_spmv_g32"; NULL: every kernel).
+ * An event pair delays the launch that follows it by a few microseconds on
+ * the device, so a timed region that needs the duration of one kernel traces
+ * only that one.  ARGCSR_EINVAL if the name has 64 characters or more. */
+ARGCSR_API argcsr_status argcsr_trace_begin_kernel(const char *name);
 ARGCSR_API argcsr_status argcsr_trace_end(void);
 ARGCSR_API int32_t argcsr_trace_kernel_count(void);
 ARGCSR_API argcsr_status argcsr_trace_kernel(int32_t index, const char **name, int64_t *launches,

@@ -139,6 +139,7 @@ _SIGNATURES = {
     "argcsr_server_stats": (ctypes.c_int, [_P] + [ctypes.POINTER(_I64)] * 4),
     "argcsr_server_destroy": (ctypes.c_int, [_P]),
     "argcsr_trace_begin": (ctypes.c_int, []),
+    "argcsr_trace_begin_kernel": (ctypes.c_int, [ctypes.c_char_p]),
     "argcsr_trace_end": (ctypes.c_int, []),
     "argcsr_trace_kernel_count": (ctypes.c_int32, []),
     "argcsr_trace_kernel": (ctypes.c_int, [_I32, ctypes.POINTER(ctypes.c_char_p),
@@ -193,6 +194,12 @@ def argcsr_version() -> str:
 
 def argcsr_trace_begin() -> None:
     _check(load_library().argcsr_trace_begin(), "argcsr_trace_begin")
+
+
+def argcsr_trace_begin_kernel(name=None) -> None:
+    """Trace only the launches of the kernel `name` (None: every kernel)."""
+    _check(load_library().argcsr_trace_begin_kernel(None if name is None else name.encode()),
+           "argcsr_trace_begin_kernel")
 
 
 def argcsr_trace_end() -> None:

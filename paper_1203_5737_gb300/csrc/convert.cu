@@ -39,6 +39,7 @@
 
 #include <mutex>
 #include <type_traits>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -707,6 +708,32 @@ argcsr_status set_smem_limits(int T) {
     return ARGCSR_OK;
 }
 
+// Pinned host copies of the totals for the two status reads (a copy into
+// pageable memory goes through a driver staging buffer and returns later),
+// kept for reuse.
+std::mutex g_totals_mu;
+std::vector<DeviceTotals *> g_totals_free;
+
+struct PinnedTotals {
+    DeviceTotals *p = nullptr;
+    PinnedTotals() {
+        {
+            std::lock_guard<std::mutex> lock(g_totals_mu);
+            if (!g_totals_free.empty()) {
+                p = g_totals_free.back();
+                g_totals_free.pop_back();
+                return;
+            }
+        }
+        if (cudaHostAlloc((void **)&p, sizeof(DeviceTotals), cudaHostAllocDefault) != cudaSuccess) p = nullptr;
+    }
+    ~PinnedTotals() {
+        if (!p) return;
+        std::lock_guard<std::mutex> lock(g_totals_mu);
+        g_totals_free.push_back(p);
+    }
+};
+
 struct Scratch {
     void *p[9] = {};
     cudaStream_t s;
@@ -801,7 +828,9 @@ extern "C" ARGCSR_API argcsr_status argcsr_create_from_csr_as(
     }
     if (st != ARGCSR_OK) return fail(st);
 
-    DeviceTotals h;
+    PinnedTotals ht;
+    if (!ht.p) return fail(ARGCSR_ENOMEM);
+    DeviceTotals &h = *ht.p;
     e = cudaMemcpyAsync(&h, tot, sizeof h, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(record_cuda(e, "conversion: read totals"));
@@ -955,7 +984,9 @@ extern "C" ARGCSR_API argcsr_status argcsr_convert_noalloc(
         default: st = set_smem_limits<128>(T); if (!st) st = Kernels<128>::run_structure(n, nnz, limit, T, numTiles, V, P1, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
     }
     if (st != ARGCSR_OK) return st;
-    DeviceTotals h;
+    PinnedTotals ht;
+    if (!ht.p) return ARGCSR_ENOMEM;
+    DeviceTotals &h = *ht.p;
     e = cudaMemcpyAsync(&h, tot, sizeof h, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return record_cuda(e, "argcsr_convert_noalloc: read totals");

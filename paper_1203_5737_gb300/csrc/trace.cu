@@ -1,4 +1,5 @@
 // Kernel tracing: CUDA event pairs around launches, summed per kernel name.
+#include <stdio.h>
 #include <string.h>
 
 #include <mutex>
@@ -12,8 +13,11 @@ namespace {
 struct Record { const char *name; cudaEvent_t start, stop; };
 struct Summary { const char *name; int64_t launches; double ms; };
 
+constexpr size_t kTracePool = 4096;   // events made ahead by argcsr_trace_begin
+
 std::mutex g_mu;
 bool g_on = false;
+char g_only[64] = "";                // non-empty: trace only the kernel of this name
 std::vector<cudaEvent_t> g_free;     // reusable events
 std::vector<Record> g_records;
 std::vector<Summary> g_summary;
@@ -30,6 +34,7 @@ cudaEvent_t take_event() {
 int trace_start(const char *name, cudaStream_t s) {
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_on) return -1;
+    if (g_only[0] && strcmp(name, g_only) != 0) return -1;
     Record r{name, take_event(), take_event()};
     if (!r.start || !r.stop) return -1;
     cudaEventRecord(r.start, s);
@@ -54,13 +59,30 @@ using namespace argcsr;
 
 extern "C" {
 
-ARGCSR_API argcsr_status argcsr_trace_begin(void) {
+static argcsr_status trace_begin(const char *only) {
     std::lock_guard<std::mutex> lock(g_mu);
+    snprintf(g_only, sizeof g_only, "%s", only ? only : "");
     for (auto &r : g_records) { g_free.push_back(r.start); g_free.push_back(r.stop); }
     g_records.clear();
     g_summary.clear();
+    // events for the first kTracePool / 2 launches are made here, so that a
+    // traced region does not pay for cudaEventCreate on its launch path
+    while (g_free.size() < kTracePool) {
+        cudaEvent_t e = nullptr;
+        const cudaError_t err = cudaEventCreate(&e);
+        if (err != cudaSuccess) return record_cuda(err, "argcsr_trace_begin");
+        g_free.push_back(e);
+    }
+    g_records.reserve(kTracePool / 2);
     g_on = true;
     return ARGCSR_OK;
+}
+
+ARGCSR_API argcsr_status argcsr_trace_begin(void) { return trace_begin(nullptr); }
+
+ARGCSR_API argcsr_status argcsr_trace_begin_kernel(const char *name) {
+    if (name && strlen(name) >= sizeof g_only) return ARGCSR_EINVAL;
+    return trace_begin(name);
 }
 
 ARGCSR_API argcsr_status argcsr_trace_end(void) {

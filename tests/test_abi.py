@@ -103,6 +103,7 @@ def test_newer_calls_check_arguments_without_gpu(lib):
                                              ctypes.byref(out)) == status
         assert out.value is None
     assert lib.argcsr_spmv_axpby(None, 1.0, None, 0.0, None, None) == api.ARGCSR_EINVAL
+    assert lib.argcsr_trace_begin_kernel(b"k" * 64) == api.ARGCSR_EINVAL
     # an allocator needs both callbacks; none restores the pool
     alloc = api.ALLOC_FN(lambda n, s, c: None)
     assert lib.argcsr_set_allocator(ctypes.cast(alloc, ctypes.c_void_p), None, None) == api.ARGCSR_EINVAL

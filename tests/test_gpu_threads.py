@@ -73,3 +73,38 @@ def test_threads_give_the_single_thread_results():
         y = alone[i][0].numpy()
         x = synth.uniform_vector(A.n_cols, i)
         assert np.all(np.abs(y - oracle.csr_spmv(A, x)) <= 1e-13 * oracle.csr_abs_spmv(A, x))
+
+
+def test_trace_all_kernels_or_one():
+    """argcsr_trace_begin records every kernel of a conversion and product;
+    argcsr_trace_begin_kernel only the one named."""
+    from paper_1203_5737_gb300 import argcsr as api
+    A = synth.random_csr(5000, 4000, 5, mean_len=8)
+    rp = torch.from_numpy(A.rowPointers).to(DEV)
+    cols = torch.from_numpy(A.columns).to(DEV)
+    vals = torch.from_numpy(A.values).to(DEV)
+    x = torch.from_numpy(synth.uniform_vector(A.n_cols, 1)).to(DEV)
+
+    def run():
+        with ArgCsrMatrix.from_csr(rp, cols, vals, A.n_cols) as M:
+            M.spmv(x)
+        torch.cuda.synchronize()
+
+    api.argcsr_trace_begin()
+    run()
+    api.argcsr_trace_end()
+    every = api.trace_summary()
+    assert {"k_tile_prepare", "k_groups", "k_fill", "k_spmv_g32"} <= set(every)
+    assert all(n == 1 and ms > 0 for n, ms in every.values())
+    api.argcsr_trace_begin_kernel("k_fill")
+    run()
+    run()
+    api.argcsr_trace_end()
+    only = api.trace_summary()
+    assert set(only) == {"k_fill"} and only["k_fill"][0] == 2
+    api.argcsr_trace_begin_kernel(None)
+    run()
+    api.argcsr_trace_end()
+    assert set(api.trace_summary()) == set(every)
+    with pytest.raises(api.ArgcsrError):
+        api.argcsr_trace_begin_kernel("k" * 64)

@@ -529,12 +529,16 @@ __device__ __forceinline__ void fill_g32(long long nGroups, int n_cols, const lo
                                          int *__restrict__ longList, long long longCap, DeviceTotals *tot) {
     const int lane = threadIdx.x & 31;
     const long long W = (long long)gridDim.x * (blockDim.x >> 5);
-    long long g = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    long long t = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     bool bad = false;
-    int4 next = g < nGroups ? gscratch[g] : make_int4(0, 0, 0, 0);
-    for (; g < nGroups; g += W) {
+    // groups in descending order: the product that follows a conversion
+    // reads them in ascending order and finds the last ones written (the
+    // first groups) still in L2
+    int4 next = t < nGroups ? gscratch[nGroups - 1 - t] : make_int4(0, 0, 0, 0);
+    for (; t < nGroups; t += W) {
+        const long long g = nGroups - 1 - t;
         const int4 s = next;
-        if (g + W < nGroups) next = gscratch[g + W];
+        if (t + W < nGroups) next = gscratch[g - W];
         const int first = s.x, size = s.y & 255, C = s.w;
         const int off = (int)(tileSlotBase[s.y >> 8] + s.z);
         const int end = lane < size ? threadsMapping[first + lane] : 0;

@@ -231,11 +231,15 @@ __device__ __forceinline__ void long_group_block(const int4 info, const int *__r
     reduce_store<MODE, AT>(m.owns ? s : AT(0), m, info.x, lane, ep, y);
 }
 
-// Register budgets: 32 with FP32 accumulation, so that 64 warps fit on an
-// SM (the gathers need every warp in flight), 40 with FP64 (48 warps; 51 for
-// V = 4, whose wider loads need more).
-template <typename VT, typename AT, int V, int MODE>
-__global__ void __launch_bounds__(256, sizeof(AT) == 4 ? 8 : (V == 4 ? 5 : 6))
+// Register budgets: 32, so that 64 warps fit on an SM (the gathers need
+// every warp in flight), with FP32 accumulation, and with FP64 for V = 1
+// when most groups take the unrolled path (WIDE false; a few registers
+// spill to L1, and 40 registers with 48 warps were 5 % slower on both bench
+// matrices).  The loop for chunks above 8 spills too much at 32, so
+// matrices whose mean chunk size is above 8 get 40 (WIDE true), as do FP64
+// V = 2; V = 4, whose wider loads need more, gets 51.
+template <typename VT, typename AT, int V, int MODE, bool WIDE>
+__global__ void __launch_bounds__(256, sizeof(AT) == 4 ? 8 : (V == 1 && !WIDE ? 8 : V == 4 ? 5 : 6))
 k_spmv_g32(long long nGroups, const int4 *__restrict__ gi, const int *__restrict__ tm,
            const int *__restrict__ cols, const VT *__restrict__ vals, const AT *__restrict__ x,
            const Epi<AT> ep, AT *__restrict__ y, const int *__restrict__ longList, int nLong) {
@@ -330,10 +334,22 @@ argcsr_status launch_typed(const argcsr_matrix *A, const void *x, const Epi<AT> 
     TraceScope t(names[A->G == 32 ? 0 : 1][MODE], s);
     const int nLong = V == 1 && A->G == 32 ? (int)A->n_long : 0;
     switch (A->G) {
-        case 32:
-            k_spmv_g32<VT, AT, V, MODE><<<(unsigned)((ng + 7) / 8 + nLong), 256, 0, s>>>(
-                ng, gi, tm, cols, vals, xx, ep, yy, A->d_longGroups, nLong);
+        case 32: {
+            const unsigned blocks = (unsigned)((ng + 7) / 8 + nLong);
+            bool wide = false;
+            // FP64, V = 1, mean chunk size S / (32 groups) above 8: mostly the looped path
+            if constexpr (sizeof(AT) == 8 && V == 1) wide = A->n_slots > 8LL * 32 * ng;
+            if constexpr (sizeof(AT) == 8 && V == 1) {
+                if (wide) {
+                    k_spmv_g32<VT, AT, V, MODE, true><<<blocks, 256, 0, s>>>(ng, gi, tm, cols, vals, xx, ep,
+                                                                             yy, A->d_longGroups, nLong);
+                    break;
+                }
+            }
+            k_spmv_g32<VT, AT, V, MODE, false><<<blocks, 256, 0, s>>>(ng, gi, tm, cols, vals, xx, ep, yy,
+                                                                      A->d_longGroups, nLong);
             break;
+        }
         case 64: k_spmv_block<64, VT, AT, V, MODE><<<(unsigned)((ng + 3) / 4), 256, 0, s>>>(ng, gi, tm, cols, vals, xx, ep, yy); break;
         default: k_spmv_block<128, VT, AT, V, MODE><<<(unsigned)((ng + 1) / 2), 256, 0, s>>>(ng, gi, tm, cols, vals, xx, ep, yy); break;
     }

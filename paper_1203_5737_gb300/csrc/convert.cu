@@ -23,16 +23,21 @@
 //      inclusive prefix (threadsMapping), and the group's slot offset inside
 //      the tile;
 //   5. k_tile_scan turns the per-tile slot totals into tile offsets;
-//   6. after one read-back of the totals, k_fill writes the group records and
-//      copies the CSR entries chunk by chunk into the interleaved arrays.
+//   6. after one read-back of the totals, k_fill writes the group records,
+//      copies the CSR entries chunk by chunk into the interleaved arrays and
+//      lists the long groups for the product; a second read-back returns
+//      the column check.
 //
 // Chunk size (Section 3, step 2).  The greedy "give one more thread to the
 // row with the greatest chunk filling until all G are placed" ends with the
 // smallest C for which sum over rows of max(1, ceil(len/C)) <= G: every
 // greedy step only splits a row whose filling is above that C, so it never
 // overshoots, and it cannot stop above it because then the rows at the
-// maximum would need fewer threads than they hold.  k_groups finds that C by
-// binary search with warp reductions.  Each row then keeps max(1,
+// maximum would need fewer threads than they hold.  k_groups finds that C
+// with one thread per group: from a lower bound it gallops upwards (for
+// small D, where the answer is usually at or just above the bound) or
+// bisects, the thread count at each trial C summed over the group's rows.
+// Each row then keeps max(1,
 // ceil(len/C)) threads; threads left over stay free (the Fig. 3 example:
 // "one thread remains free").
 #include <stdio.h>

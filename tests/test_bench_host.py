@@ -112,3 +112,29 @@ def test_reference_arm_other_ranks_do_no_work(monkeypatch, capsys):
     monkeypatch.setenv("WORLD_SIZE", "2")
     bench.main(["--impl", "reference", "--steps", "1", "--warmup", "3"])
     assert capsys.readouterr().out == ""
+
+
+def test_profile_figures_follow_the_kernel_sources(tmp_path, monkeypatch):
+    """ncu figures are reported only for the sources they were taken on: a
+    line keyed by the current digest is read, one keyed by another is not."""
+    digest = bench.kernel_source_digest("k_spmv_g32")
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.txt").write_text(
+        "# comment\n"
+        f"k_spmv_g32 bench 123456 {digest}\n"
+        "k_fill bench 999 0000000000000000\n")
+    (tmp_path / "profiles" / "limits.txt").write_text(
+        f"k_spmv_g32 l1tex_throughput_pct 31.5 80.5 {digest}\n"
+        "k_spmv_g32 fp64_pipe_active_pct 1.0 2.0 0000000000000000\n")
+    csrc = os.path.join(bench.ROOT, "paper_1203_5737_gb300", "csrc")
+    real_root = bench.ROOT
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    # the digest still has to be taken from the real sources
+    (tmp_path / "paper_1203_5737_gb300").mkdir()
+    os.symlink(csrc, tmp_path / "paper_1203_5737_gb300" / "csrc")
+    assert bench.kernel_source_digest("k_spmv_g32") == digest
+    assert bench.ncu_traffic("k_spmv_g32") == 123456
+    assert bench.ncu_traffic("k_fill") is None
+    assert bench.ncu_limits("k_spmv_g32") == {"l1tex_throughput_pct": {"laplacian": 31.5, "lognormal": 80.5}}
+    assert bench.ncu_traffic("k_unknown") is None
+    monkeypatch.setattr(bench, "ROOT", real_root)

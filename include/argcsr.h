@@ -436,8 +436,10 @@ ARGCSR_API argcsr_status argcsr_server_destroy(argcsr_server_t server);
  * memory cap, or a latency-critical loop where cudaMalloc/cudaFree would
  * stall the device.  Such callers can still size and own their outputs.
  *
- * What it does not do: call cudaMalloc, cudaFree, a memory pool, or any
- * allocating library routine.  All intermediate arrays live in one
+ * What it does not do: call cudaMalloc, cudaFree, cudaHostAlloc, a memory
+ * pool, or any allocating library routine, on the device or the host (the
+ * sizes come back through a copy into a local variable).  All intermediate
+ * arrays live in one
  * file-scope __device__ array of ARGCSR_NOALLOC_SCRATCH_BYTES bytes, which
  * every GPU that loads this library holds until the process exits.  That
  * caps the matrix at ARGCSR_NOALLOC_MAX_ROWS rows; more rows return
@@ -466,7 +468,7 @@ ARGCSR_API argcsr_status argcsr_server_destroy(argcsr_server_t server);
  * argcsr_create_from_csr.
  * ------------------------------------------------------------------------ */
 #define ARGCSR_NOALLOC_MAX_ROWS 1048576
-#define ARGCSR_NOALLOC_SCRATCH_BYTES 17996032
+#define ARGCSR_NOALLOC_SCRATCH_BYTES 18166016
 ARGCSR_API argcsr_status argcsr_convert_noalloc(
     int32_t n_rows, int32_t n_cols, int64_t nnz,
     const int32_t *d_rowPointers, const int32_t *d_columns, const void *d_values,

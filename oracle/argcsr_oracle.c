@@ -41,7 +41,7 @@
  *       the Fig. 3 example (15 nonzeros, 12 threads, D = 1) is one group.
  *   A2  after the greedy fixes chunkSize C, every row keeps only
  *       max(1, ceil(len / C)) threads; leftover threads stay free (Fig. 3:
- *       "4 threads ... one thread remains free").
+ *       the last row gets four threads and one of the twelve is left over).
  *   A3  greedy ties go to the lowest row index (C does not depend on it).
  *   A4  an empty row gets one all-padding chunk; a group without nonzeros
  *       has chunkSize 0 and no slots.

@@ -38,8 +38,8 @@
 // small D, where the answer is usually at or just above the bound) or
 // bisects, the thread count at each trial C summed over the group's rows.
 // Each row then keeps max(1,
-// ceil(len/C)) threads; threads left over stay free (the Fig. 3 example:
-// "one thread remains free").
+// ceil(len/C)) threads; threads left over stay free (in the Fig. 3 example
+// the last row takes four threads and one of the twelve is left over).
 #include <stdio.h>
 
 #include <mutex>
@@ -899,7 +899,7 @@ extern "C" ARGCSR_API argcsr_status argcsr_create_from_csr_as(
 namespace argcsr {
 namespace {
 
-constexpr int kNoallocTile = 4096;                               // T for n <= 2^25
+constexpr int kNoallocTile = 2048;   // the tile of argcsr_create_from_csr for n <= 2^25
 constexpr int kNoallocMaxTiles = ARGCSR_NOALLOC_MAX_ROWS / kNoallocTile;
 constexpr size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 // carve-up of the scratch array (each part 256-byte aligned)
@@ -928,7 +928,10 @@ argcsr_status noalloc_scratch(unsigned char **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return record_cuda(e, "cudaGetDevice");
-    if (dev < 0 || dev >= 64) return ARGCSR_ENOTSUP;
+    if (dev < 0 || dev >= 64) {
+        set_error_message("argcsr_convert_noalloc: device ordinal above 63");
+        return ARGCSR_ENOTSUP;
+    }
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     if (!g_noalloc_ptr[dev]) {
         void *p = nullptr;
@@ -949,23 +952,32 @@ extern "C" ARGCSR_API argcsr_status argcsr_convert_noalloc(
     int32_t *d_groupInfo, int64_t group_capacity, int32_t *d_threadsMapping,
     int32_t *d_out_columns, void *d_out_values, int64_t slot_capacity, int64_t *h_n_groups,
     int64_t *h_n_slots, argcsr_stream_t stream) {
-    if (!h_n_groups || !h_n_slots) return ARGCSR_EINVAL;
+    // every failure below leaves a message for argcsr_last_error_message()
+    auto fail = [](argcsr_status st, const char *why) {
+        set_error_message(why);
+        return st;
+    };
+    if (!h_n_groups || !h_n_slots) return fail(ARGCSR_EINVAL, "argcsr_convert_noalloc: null size outputs");
     *h_n_groups = 0;
     *h_n_slots = 0;
-    if (!params || n_rows < 0 || n_cols < 0 || nnz < 0 || nnz > 0x7fffffffLL) return ARGCSR_EINVAL;
-    if (n_rows > ARGCSR_NOALLOC_MAX_ROWS) {
-        set_error_message("argcsr_convert_noalloc: n_rows exceeds ARGCSR_NOALLOC_MAX_ROWS");
-        return ARGCSR_EINVAL;
-    }
+    if (!params || n_rows < 0 || n_cols < 0 || nnz < 0 || nnz > 0x7fffffffLL)
+        return fail(ARGCSR_EINVAL, "argcsr_convert_noalloc: bad sizes or null params");
+    if (n_rows > ARGCSR_NOALLOC_MAX_ROWS)
+        return fail(ARGCSR_EINVAL, "argcsr_convert_noalloc: n_rows exceeds ARGCSR_NOALLOC_MAX_ROWS");
     const int G = params->group_size, D = params->desired_chunk_size, V = params->vec_width;
     const int P1 = params->one_thread_per_row;
-    if ((G != 32 && G != 64 && G != 128) || D < 1 || (V != 1 && V != 2 && V != 4)) return ARGCSR_EINVAL;
-    if (P1 != 0 && P1 != 1) return ARGCSR_EINVAL;
-    if (dtype != ARGCSR_F64 && dtype != ARGCSR_F32 && dtype != ARGCSR_BF16) return ARGCSR_EINVAL;
-    if (!d_rowPointers || (nnz > 0 && (!d_columns || !d_values))) return ARGCSR_EINVAL;
-    if (n_rows == 0) return nnz == 0 ? ARGCSR_OK : ARGCSR_EINVAL;
-    if (!d_threadsMapping || group_capacity < 0 || slot_capacity < 0) return ARGCSR_EINVAL;
-    if (reinterpret_cast<uintptr_t>(d_groupInfo) % 16) return ARGCSR_EINVAL;  // int4 records
+    if ((G != 32 && G != 64 && G != 128) || D < 1 || (V != 1 && V != 2 && V != 4) || (P1 != 0 && P1 != 1))
+        return fail(ARGCSR_EINVAL, "argcsr_convert_noalloc: bad group size, chunk size, vector width or mode");
+    if (dtype != ARGCSR_F64 && dtype != ARGCSR_F32 && dtype != ARGCSR_BF16)
+        return fail(ARGCSR_EINVAL, "argcsr_convert_noalloc: bad dtype");
+    if (!d_rowPointers || (nnz > 0 && (!d_columns || !d_values)))
+        return fail(ARGCSR_EINVAL, "argcsr_convert_noalloc: null input array");
+    if (n_rows == 0)
+        return nnz == 0 ? ARGCSR_OK : fail(ARGCSR_EINVAL, "argcsr_convert_noalloc: nnz > 0 with no rows");
+    if (!d_threadsMapping || group_capacity < 0 || slot_capacity < 0)
+        return fail(ARGCSR_EINVAL, "argcsr_convert_noalloc: null threadsMapping or negative capacity");
+    if (reinterpret_cast<uintptr_t>(d_groupInfo) % 16)   // int4 records
+        return fail(ARGCSR_EINVAL, "argcsr_convert_noalloc: d_groupInfo is not 16-byte aligned");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
 
     unsigned char *base = nullptr;
@@ -993,22 +1005,24 @@ extern "C" ARGCSR_API argcsr_status argcsr_convert_noalloc(
         default: st = set_smem_limits<128>(T); if (!st) st = Kernels<128>::run_structure(n, nnz, limit, T, numTiles, V, P1, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
     }
     if (st != ARGCSR_OK) return st;
-    PinnedTotals ht;
-    if (!ht.p) return ARGCSR_ENOMEM;
-    DeviceTotals &h = *ht.p;
+    // the totals come back into this stack copy: a copy into pageable
+    // memory returns once it is done, and the synchronisation orders it in
+    // any case; no pinned buffer is taken (allocating one is what this entry
+    // point exists to avoid)
+    DeviceTotals h{};
     e = cudaMemcpyAsync(&h, tot, sizeof h, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return record_cuda(e, "argcsr_convert_noalloc: read totals");
-    if (h.status & kBadRowPointers) return ARGCSR_EINVAL;
-    if (h.status & kSlotOverflow) return ARGCSR_EOVERFLOW;
+    if (h.status & kBadRowPointers)
+        return fail(ARGCSR_EINVAL, "argcsr_convert_noalloc: rowPointers not monotone from 0 to nnz");
+    if (h.status & kSlotOverflow)
+        return fail(ARGCSR_EOVERFLOW, "argcsr_convert_noalloc: more than 2^31 - 1 slots");
     *h_n_groups = h.n_groups;
     *h_n_slots = h.n_slots;
-    if (h.n_groups > group_capacity || h.n_slots > slot_capacity) {
-        set_error_message("argcsr_convert_noalloc: output capacity too small (required sizes returned)");
-        return ARGCSR_EINVAL;
-    }
+    if (h.n_groups > group_capacity || h.n_slots > slot_capacity)
+        return fail(ARGCSR_EINVAL, "argcsr_convert_noalloc: output capacity too small (required sizes returned)");
     if ((h.n_groups > 0 && !d_groupInfo) || (h.n_slots > 0 && (!d_out_columns || !d_out_values)))
-        return ARGCSR_EINVAL;
+        return fail(ARGCSR_EINVAL, "argcsr_convert_noalloc: null output array");
     int4 *gi = reinterpret_cast<int4 *>(d_groupInfo);
     const size_t es = dtype_size(dtype);
 #define FILL(GG, VT)                                                                              \
@@ -1024,6 +1038,6 @@ extern "C" ARGCSR_API argcsr_status argcsr_convert_noalloc(
     e = cudaMemcpyAsync(&h, tot, sizeof h, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return record_cuda(e, "argcsr_convert_noalloc: read status");
-    if (h.status & kBadColumn) return ARGCSR_EINVAL;
+    if (h.status & kBadColumn) return fail(ARGCSR_EINVAL, "argcsr_convert_noalloc: column index out of range");
     return ARGCSR_OK;
 }

@@ -130,3 +130,17 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(api, "_lib", None)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         api.load_library(str(tmp_path / "libargcsr.so"))
+
+
+def test_noalloc_entry_point_names_no_allocating_call():
+    """argcsr_convert_noalloc and the scratch look-up it uses take no device or
+    host memory: their source names no allocating routine (the shared kernel
+    launchers they call only launch kernels)."""
+    src = open(os.path.join(ROOT, "paper_1203_5737_gb300", "csrc", "convert.cu")).read()
+    body = src[src.index('extern "C" ARGCSR_API argcsr_status argcsr_convert_noalloc('):]
+    helper = src[src.index("argcsr_status noalloc_scratch("):src.index("}  // namespace", src.index(
+        "argcsr_status noalloc_scratch("))]
+    code = "\n".join(line.split("//")[0] for line in (body + helper).splitlines())
+    for name in ("cudaMalloc", "cudaFree", "cudaHostAlloc", "cudaMallocHost", "cudaMallocAsync",
+                 "PinnedTotals", "pool_alloc", "malloc(", "new ", "std::vector", "std::string"):
+        assert name not in code, name

@@ -8,9 +8,15 @@ tests call it through the C ABI and compare what it writes with what the
 allocating entry point (argcsr_create_from_csr + argcsr_export) produces,
 bit for bit, on two calls in a row.  The file is named to run last.
 """
+import os
+import subprocess
+import sys
+import textwrap
+
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 torch = pytest.importorskip("torch")
@@ -128,3 +134,102 @@ def test_no_device_memory_is_taken():
     assert torch.cuda.mem_get_info()[0] >= free_before
     assert np.array_equal(gi[:ng].cpu().numpy(), ref["groupInfo"])
     assert np.array_equal(oc.cpu().numpy(), ref["columns"])
+
+
+def test_wide_groups_and_vectors():
+    # G = 128 with V = 4 and a larger chunk size, and G = 64 with V = 4: the
+    # no-alloc path uses the shared-memory limits of these group sizes
+    A = synth.random_csr(120_000, 70_000, 21, mean_len=11, p_empty=0.1, n_huge=4, huge_len=5000)
+    rp, cols, vals = _device_csr(A)
+    for G, D, V in ((128, 12, 4), (64, 7, 4), (128, 1, 1)):
+        _same(_noalloc(A, rp, cols, vals, G, D, V, api.ARGCSR_F64), _reference(A, rp, cols, vals, G, D, V))
+
+
+def test_matches_the_oracle_directly():
+    A = synth.random_csr(40_000, 30_000, 23, mean_len=8, p_empty=0.1, n_huge=2, huge_len=2500)
+    rp, cols, vals = _device_csr(A)
+    got = _noalloc(A, rp, cols, vals, 32, 4, 1, api.ARGCSR_F64)
+    ref = oracle.convert(A, 32, 4)
+    assert np.array_equal(got["groupInfo"], ref.groupInfo)
+    assert np.array_equal(got["threadsMapping"], ref.threadsMapping)
+    assert np.array_equal(got["columns"], ref.columns)
+    assert np.array_equal(got["values"], ref.values)
+
+
+def _status_and_message(n_rows, n_cols, nnz, rp, cols, vals, G=32, D=4, V=1, cap=(0, 0)):
+    s = torch.cuda.current_stream().cuda_stream
+    tm = torch.empty(max(1, n_rows), dtype=torch.int32, device=DEV)
+    gi = torch.empty((max(1, cap[0]), 4), dtype=torch.int32, device=DEV)
+    oc = torch.empty(max(1, cap[1]), dtype=torch.int32, device=DEV)
+    ov = torch.empty(max(1, cap[1]), dtype=torch.float64, device=DEV)
+    st, _, _ = api.argcsr_convert_noalloc(n_rows, n_cols, nnz, rp.data_ptr(), cols.data_ptr(),
+                                          vals.data_ptr(), api.ARGCSR_F64, G, D, V, gi.data_ptr(),
+                                          cap[0], tm.data_ptr(), oc.data_ptr(), ov.data_ptr(), cap[1], s)
+    return st, api.argcsr_last_error_message()
+
+
+def test_invalid_inputs_return_their_status():
+    A = synth.random_csr(5000, 400, 4, mean_len=5, p_empty=0.0)
+    rp, cols, vals = _device_csr(A)
+    cap = (A.n_rows, 8 * A.nnz)
+    bad = rp.clone()
+    bad[100], bad[101] = rp[101] + 3, rp[100]            # not monotone
+    st, msg = _status_and_message(A.n_rows, A.n_cols, A.nnz, bad, cols, vals, cap=cap)
+    assert st == api.ARGCSR_EINVAL and "rowPointers" in msg
+    for badcol in (-1, A.n_cols):                         # a column out of range
+        c2 = cols.clone()
+        c2[A.nnz // 2] = badcol
+        st, msg = _status_and_message(A.n_rows, A.n_cols, A.nnz, rp, c2, vals, cap=cap)
+        assert st == api.ARGCSR_EINVAL and "column" in msg
+    # more than 2^31 - 1 slots: one 128-row group whose last row is 2^24 long
+    rp_np, D = synth.pathological_overflow_rowpointers(128)
+    nnz = int(rp_np[-1])
+    rpo = torch.from_numpy(rp_np).to(DEV)
+    co = torch.zeros(nnz, dtype=torch.int32, device=DEV)
+    vo = torch.zeros(nnz, dtype=torch.float64, device=DEV)
+    st, msg = _status_and_message(128, 1, nnz, rpo, co, vo, G=128, D=D)
+    assert st == api.ARGCSR_EOVERFLOW and "2^31" in msg
+    del co, vo
+    torch.cuda.empty_cache()
+    # the entry point still works after the rejections
+    _same(_noalloc(A, rp, cols, vals, 32, 4, 1, api.ARGCSR_F64), _reference(A, rp, cols, vals, 32, 4, 1))
+
+
+_FIRST_CALL = textwrap.dedent("""
+    import sys
+    sys.path.insert(0, {root!r})
+    import numpy as np, torch
+    import oracle, synth
+    from paper_1203_5737_gb300 import argcsr as api
+    A = synth.random_csr(30_000, 20_000, 31, mean_len=7, p_empty=0.1, n_huge=2, huge_len=2000)
+    rp = torch.from_numpy(A.rowPointers).cuda()
+    cols = torch.from_numpy(A.columns).cuda()
+    vals = torch.from_numpy(A.values).cuda()
+    ref = oracle.convert(A, 32, 4)
+    tm = torch.empty(A.n_rows, dtype=torch.int32, device="cuda")
+    gi = torch.empty((ref.n_groups, 4), dtype=torch.int32, device="cuda")
+    oc = torch.empty(ref.n_slots, dtype=torch.int32, device="cuda")
+    ov = torch.empty(ref.n_slots, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream().cuda_stream
+    # the first call of the library in this process is the no-alloc one
+    st, ng, ns = api.argcsr_convert_noalloc(A.n_rows, A.n_cols, A.nnz, rp.data_ptr(), cols.data_ptr(),
+                                            vals.data_ptr(), api.ARGCSR_F64, 32, 4, 1, gi.data_ptr(),
+                                            ref.n_groups, tm.data_ptr(), oc.data_ptr(), ov.data_ptr(),
+                                            ref.n_slots, s)
+    assert st == api.ARGCSR_OK, st
+    assert (ng, ns) == (ref.n_groups, ref.n_slots)
+    assert np.array_equal(gi.cpu().numpy(), ref.groupInfo)
+    assert np.array_equal(tm.cpu().numpy(), ref.threadsMapping)
+    assert np.array_equal(oc.cpu().numpy(), ref.columns)
+    assert np.array_equal(ov.cpu().numpy(), ref.values)
+    print("first call ok")
+""")
+
+
+def test_first_call_in_a_fresh_process():
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _FIRST_CALL.format(root=root)], capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "first call ok" in r.stdout

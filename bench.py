@@ -1,23 +1,29 @@
 #!/usr/bin/env python3
 """Benchmark of the ARG-CSR hot path on GB300.
 
-One step = the whole hot path over the uneven-rows FP64 workload: for each
-of its two matrices -- lognormal(2.3, 1.2) row lengths with n = 2,000,000
-and the 7-point Laplacian on a 128^3 grid -- CSR -> ARG-CSR conversion
-(G = 32) followed by one SpMV y = A x, then the handle is freed.  The CSR
-inputs and x are resident in HBM before the timed region starts.
+Default line (``python bench.py``): the uneven-rows FP64 workload, two
+matrices -- lognormal(2.3, 1.2) row lengths with n = 2,000,000 and the
+7-point Laplacian on a 128^3 grid -- converted once from CSR to ARG-CSR
+(G = 32, desiredChunkSize chosen per matrix by the library's autotuner,
+untimed), resident in HBM with x.  One step = y = A x for both matrices
+(the paper's measured operation, Section 5).
 
-value = algorithmic bytes of the step / step time, where
-  conversion: 4(n+1) + nnz(4+8)            (read the CSR arrays)
-            + 16 groups + 4 n + S (4+8)    (write groupInfo, threadsMapping
-                                            and the S padded slots)
-  SpMV:       nnz(8+4) + 8 n_cols + 8 n + 4 n + 16 groups
-              (values + columns + x + y + threadsMapping + groupInfo;
-               padding not counted)
-The SpMV-only rate (the paper's measured kernel) is reported under "spmv",
-beside the plain CSR kernel and cuSPARSE on the same matrices.
+value = algorithmic bytes of the step / step time, per SpMV
+  nnz (8 + 4) + 8 n_cols + 8 n + 4 n + 16 groups
+  (values + columns + x + y + threadsMapping + groupInfo; padding not counted)
+
+The same line carries, each measured in this run: the roofline of k_spmv_g32
+(and, as a second entry, of the conversion's k_fill) with the ceilings that
+the SpMV's memory accesses alone set (measured by a probe kernel); the
+conversion + SpMV step; per-matrix SpMV beside the plain CSR kernels and
+cuSPARSE; FP32/BF16 storage with the error against the FP64 oracle; the
+mixed-precision CG (3D Poisson 160^3) against plain FP64 CSR CG; a compact
+serving run (64-matrix pool) against plain FP64 CSR served first come first
+served; the end-to-end rate with x and y in host memory; and the oracle on
+the host cores, on one core and on all of them.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workload uneven_fp64|cg_poisson160|batched4096|serving]
 
 With --gpus N > 1 (launched by torchrun) every rank runs an independent
 replica of the workload on its own GPU (the path needs no exchange); value
@@ -29,10 +35,13 @@ import argparse
 import hashlib
 import json
 import os
+import platform
+import re
 import statistics
 import subprocess
 import sys
 import tempfile
+import threading
 import time
 
 import numpy as np
@@ -45,29 +54,31 @@ import synth  # noqa: E402
 
 METRIC = "ARG-CSR SpMV GB/s (% HBM peak) vs plain CSR; served CG solves/s, p99 latency"
 WORKLOAD = ("uneven rows FP64: lognormal(2.3,1.2) n=2,000,000 + 3D 7-point Laplacian 128^3; "
-            "CSR->ARG-CSR (G=32) + SpMV per matrix")
+            "ARG-CSR (G=32, D autotuned per matrix) resident in HBM; step = SpMV of both")
 GROUP_SIZE = 32
-MATRICES = (("lognormal_2m", 4), ("laplace3d_128", 8))   # (workload, desiredChunkSize)
+MATRICES = ("lognormal_2m", "laplace3d_128")
+FALLBACK_D = {"lognormal_2m": 8, "laplace3d_128": 8}
 SV = 8   # bytes per stored value (FP64)
 SX = 8   # bytes per x / y element
 FALLBACK_HBM_GBS = 6800.0
 L2_BYTES = 129 * 2 ** 20
+DTYPE_BYTES = {0: 8, 1: 4, 2: 2}   # ARGCSR_F64, F32, BF16 stored value sizes
 
 
 # ---------------------------------------------------------------------------
 # byte model
 # ---------------------------------------------------------------------------
 
-def conversion_bytes(n, nnz, groups, slots):
-    return 4 * (n + 1) + nnz * (4 + SV) + 16 * groups + 4 * n + slots * (4 + SV)
+def conversion_bytes(n, nnz, groups, slots, sv=SV):
+    return 4 * (n + 1) + nnz * (4 + sv) + 16 * groups + 4 * n + slots * (4 + sv)
 
 
-def spmv_bytes(n, n_cols, nnz, groups):
-    return nnz * (SV + 4) + n_cols * SX + n * SX + 4 * n + 16 * groups
+def spmv_bytes(n, n_cols, nnz, groups, sv=SV, sx=SX):
+    return nnz * (sv + 4) + n_cols * sx + n * sx + 4 * n + 16 * groups
 
 
-def csr_spmv_bytes(n, n_cols, nnz):
-    return nnz * (SV + 4) + n_cols * SX + n * SX + 4 * (n + 1)
+def csr_spmv_bytes(n, n_cols, nnz, sv=SV, sx=SX):
+    return nnz * (sv + 4) + n_cols * sx + n * sx + 4 * (n + 1)
 
 
 def kernel_bytes(kernel, n, n_cols, nnz, groups, slots):
@@ -79,7 +90,6 @@ def kernel_bytes(kernel, n, n_cols, nnz, groups, slots):
         "k_spmv_g32": spmv_bytes(n, n_cols, nnz, groups),
         "k_spmv_block": spmv_bytes(n, n_cols, nnz, groups),
     }.get(kernel, 0)
-
 
 # ---------------------------------------------------------------------------
 # multi-rank plumbing (replicas only)
@@ -195,53 +205,82 @@ KERNEL_SOURCES = {"k_fill": ("convert.cu", "device.cuh"),
                   "k_spmv_g32": ("spmv.cu", "device.cuh")}
 
 
+def strip_comments(text: str) -> str:
+    """C/C++ source without comments and blank lines, so that an edit of
+    comments alone leaves a kernel's digest unchanged."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = (re.sub(r"//.*", "", line).rstrip() for line in text.splitlines())
+    return "\n".join(line for line in lines if line.strip())
+
+
 def kernel_source_digest(kernel):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1203_5737_gb300", "csrc")
     for name in KERNEL_SOURCES.get(kernel, ()):
-        with open(os.path.join(csrc, name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(csrc, name)) as f:
+            h.update(strip_comments(f.read()).encode())
     return h.hexdigest()[:16]
 
 
-def ncu_limits(kernel):
-    """Unit utilisation of `kernel` from profiles/limits.txt (same digest
-    rule as the traffic), as {metric: {"laplace3d_128_like": %, "lognormal_like": %}}."""
+def _profile_rows(name, kernel, ncols):
+    """Rows of profiles/<name> for `kernel` taken on its current sources."""
     if kernel not in KERNEL_SOURCES:
-        return None
+        return []
     digest = kernel_source_digest(kernel)
-    out = {}
+    rows = []
     try:
-        with open(os.path.join(ROOT, "profiles", "limits.txt")) as f:
+        with open(os.path.join(ROOT, "profiles", name)) as f:
             for line in f:
                 if line.startswith("#") or not line.strip():
                     continue
-                k, metric, lap, logn, dig = line.split()[:5]
-                if k == kernel and dig == digest:
-                    out[metric] = {"laplacian": float(lap), "lognormal": float(logn)}
+                parts = line.split()
+                if len(parts) >= ncols and parts[0] == kernel and parts[ncols - 1] == digest:
+                    rows.append(parts[:ncols])
     except OSError:
-        return None
+        pass
+    return rows
+
+
+def ncu_limits(kernel):
+    """Unit utilisation of `kernel` from profiles/limits.txt, as
+    {metric: {workload: %}}, if taken on the current sources (else None)."""
+    out = {}
+    for _, metric, wl, pct, _ in _profile_rows("limits.txt", kernel, 5):
+        out.setdefault(metric, {})[wl] = float(pct)
     return out or None
 
 
-def ncu_traffic(kernel):
-    """DRAM bytes per launch from profiles/traffic.txt, if they were taken on
-    the current sources of that kernel (else None)."""
-    if kernel not in KERNEL_SOURCES:
-        return None
-    path = os.path.join(ROOT, "profiles", "traffic.txt")
-    digest = kernel_source_digest(kernel)
+def ncu_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from
+    profiles/traffic.txt, if taken on the current sources (else None)."""
+    for _, wl, nbytes, _ in _profile_rows("traffic.txt", kernel, 4):
+        if wl == workload:
+            return float(nbytes)
+    return None
+
+
+def host_description():
+    model = None
     try:
-        with open(path) as f:
+        with open("/proc/cpuinfo") as f:
             for line in f:
-                if line.startswith("#") or not line.strip():
-                    continue
-                k, wl, nbytes, dig = line.split()[:4]
-                if k == kernel and wl == "bench" and dig == digest:
-                    return float(nbytes)
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
     except OSError:
         pass
-    return None
+    if not model:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.processor() or "unknown",
+            "machine": platform.machine()}
 
 
 # ---------------------------------------------------------------------------
@@ -252,10 +291,10 @@ class Mat:
     pass
 
 
-def prepare(name, D, dev, torch, pinned=False):
+def prepare(name, dev, torch):
     A, x = synth.workload(name)
     m = Mat()
-    m.name, m.D, m.A = name, D, A
+    m.name, m.A = name, A
     m.n, m.n_cols, m.nnz = A.n_rows, A.n_cols, A.nnz
     m.rp = torch.from_numpy(A.rowPointers).to(dev)
     m.cols = torch.from_numpy(A.columns).to(dev)
@@ -263,13 +302,36 @@ def prepare(name, D, dev, torch, pinned=False):
     m.x = torch.from_numpy(x).to(dev)
     m.y = torch.empty(m.n, dtype=torch.float64, device=dev)
     m.x_np = x
-    if pinned:
-        m.h_rp = torch.from_numpy(A.rowPointers).pin_memory()
-        m.h_cols = torch.from_numpy(A.columns).pin_memory()
-        m.h_vals = torch.from_numpy(A.values).pin_memory()
-        m.h_x = torch.from_numpy(x).pin_memory()
-        m.h_y = torch.empty(m.n, dtype=torch.float64).pin_memory()
+    m.h_rp = torch.from_numpy(A.rowPointers).pin_memory()
+    m.h_cols = torch.from_numpy(A.columns).pin_memory()
+    m.h_vals = torch.from_numpy(A.values).pin_memory()
+    m.h_x = torch.from_numpy(x).pin_memory()
+    m.h_y = torch.empty(m.n, dtype=torch.float64).pin_memory()
     return m
+
+
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _time_us(torch, stream, fn, reps, rounds=5):
+    """Median over `rounds` of the mean time of `reps` back-to-back calls."""
+    for _ in range(3):
+        fn()
+    ts = []
+    for _ in range(rounds):
+        a, b = _events(torch)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b) * 1e3 / reps)
+    return statistics.median(ts)
+
+
+def _gbs(nbytes, us):
+    return nbytes / (us * 1e-6) / 1e9
 
 
 def run_ours(args):
@@ -280,6 +342,11 @@ def run_ours(args):
     rank, world, local = dist_env()
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU (there is no CPU fallback)")
+    # host-side inputs of the serving block first (its generator pool is
+    # spawned, but nothing is lost by building it before CUDA starts)
+    pool = None
+    if not args.no_serving:
+        pool = synth.serving_pool(64, seed=0, workers=min(16, os.cpu_count() or 1))
     torch.cuda.set_device(local)
     dist_init(world, "nccl")
     build.build()
@@ -287,151 +354,246 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     s = stream.cuda_stream
-    mats = [prepare(name, D, dev, torch, pinned=True) for name, D in MATRICES]
+    peak, peak_kind = measured_hbm_peak()
+    mats = [prepare(name, dev, torch) for name in MATRICES]
 
-    def convert(m, src=None):
+    def convert(m, D, storage=None, src=None, **kw):
         rp, cols, vals = src or (m.rp, m.cols, m.vals)
-        return api.argcsr_create_from_csr(m.n, m.n_cols, m.nnz, rp.data_ptr(), cols.data_ptr(),
-                                          vals.data_ptr(), api.ARGCSR_F64, GROUP_SIZE, m.D, 1, s)
+        if storage is None:
+            return api.argcsr_create_from_csr(m.n, m.n_cols, m.nnz, rp.data_ptr(), cols.data_ptr(),
+                                              vals.data_ptr(), api.ARGCSR_F64, GROUP_SIZE, D, 1, s, **kw)
+        return api.argcsr_create_from_csr_as(m.n, m.n_cols, m.nnz, rp.data_ptr(), cols.data_ptr(),
+                                             vals.data_ptr(), api.ARGCSR_F64, storage, GROUP_SIZE, D, 1, s)
+
+    # desiredChunkSize per matrix from the library's autotuner (G = 32, the
+    # paper's candidates of D); untimed set-up, like the conversion itself
+    for m in mats:
+        if args.no_autotune:
+            m.D, m.tune_us = FALLBACK_D[m.name], None
+        else:
+            (G, m.D, _, _), m.tune_us = api.argcsr_autotune(
+                m.n, m.n_cols, m.nnz, m.rp.data_ptr(), m.cols.data_ptr(), m.vals.data_ptr(),
+                api.ARGCSR_F64, 1, 1, 10, s)
+        m.h = convert(m, m.D)
+        info = api.argcsr_info(m.h)
+        m.groups, m.slots = info.n_groups, info.n_slots
+        m.spmv_bytes = spmv_bytes(m.n, m.n_cols, m.nnz, m.groups)
+    step_bytes = sum(m.spmv_bytes for m in mats)
 
     def step():
         for m in mats:
-            h = convert(m)
-            api.argcsr_spmv(h, m.x.data_ptr(), m.y.data_ptr(), s)
-            api.argcsr_destroy(h, s)
+            api.argcsr_spmv(m.h, m.x.data_ptr(), m.y.data_ptr(), s)
 
-    # sizes of the converted matrices (identical every step)
-    for m in mats:
-        h = convert(m)
-        info = api.argcsr_info(h)
-        m.groups, m.slots = info.n_groups, info.n_slots
-        api.argcsr_destroy(h, s)
-        m.step_bytes = (conversion_bytes(m.n, m.nnz, m.groups, m.slots)
-                        + spmv_bytes(m.n, m.n_cols, m.nnz, m.groups))
-    step_bytes = sum(m.step_bytes for m in mats)
-
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    # kernel shares from a traced pass of the same steps before the timed
-    # region: an event pair around every launch adds about 50 us to a step,
-    # so the timed region traces only the dominant kernel
-    api.argcsr_trace_begin()
-    for _ in range(args.steps):
-        step()
-    torch.cuda.synchronize()
-    api.argcsr_trace_end()
-    shares = api.trace_summary()
-    dominant = max(shares, key=lambda k: shares[k][1])
     barrier(world)
     launches0 = api.argcsr_launch_count()
-    sampler = ClockSampler(torch.cuda.current_device())
-    sampler.start()
-    api.argcsr_trace_begin_kernel(dominant)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0, e1 = _events(torch)
     e0.record(stream)
     for _ in range(args.steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
-    api.argcsr_trace_end()
-    clocks = sampler.stop()
-    barrier(world)
     launches = api.argcsr_launch_count() - launches0
+    # the timed region is short (a few ms): the clock samples are taken over
+    # it and a soak of the same step of at least 0.6 s right after it
+    t_soak = time.perf_counter()
+    while time.perf_counter() - t_soak < 0.6:
+        for _ in range(50):
+            step()
+        torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if clocks is not None:
+        clocks["window"] = "warm-up, timed region and a 0.6 s soak of the same step"
+    barrier(world)
     ms = e0.elapsed_time(e1)
     ms_max = reduce_max(ms, world, dev)
-    total_bytes = reduce_sum(step_bytes * args.steps, world, dev)
-    value = total_bytes / (ms_max * 1e-3) / 1e9
-    trace = api.trace_summary()
+    value = reduce_sum(step_bytes * args.steps, world, dev) / (ms_max * 1e-3) / 1e9
 
-    # roofline of the dominant kernel (largest share of the traced pass),
-    # timed by its own events inside the timed region
-    peak, peak_kind = measured_hbm_peak()
-    launches_k, ms_k = trace[dominant]
-    per_step = sum(kernel_bytes(dominant, m.n, m.n_cols, m.nnz, m.groups, m.slots) for m in mats)
-    kbytes = per_step * args.steps
-    achieved = kbytes / (ms_k * 1e-3) / 1e9
-    traffic = ncu_traffic(dominant)
-    roofline = {"bound": "hbm", "kernel": dominant, "achieved": round(achieved, 1),
-                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": traffic, "peak_source": peak_kind,
-                "bytes_per_launch": round(kbytes / launches_k),
-                "avg_launch_us": round(ms_k * 1e3 / launches_k, 2),
-                "other_limits_ncu": ncu_limits(dominant)}
+    # per matrix: the SpMV alone, and the ceilings its memory accesses set
+    # (argcsr_probe_gather: the same group records, streams and gathers
+    # with no arithmetic; mode 0 columns + x gathers, 1 columns + values +
+    # x gathers, 2 columns only)
+    reps = max(20, args.steps * 5)
+    spmv, probe = {}, {}
+    for m in mats:
+        xp, yp = m.x.data_ptr(), m.y.data_ptr()
+        m.us = _time_us(torch, stream, lambda: api.argcsr_spmv(m.h, xp, yp, s), reps)
+        pr = {f"mode{md}": round(_time_us(torch, stream, lambda: api.argcsr_probe_gather(m.h, xp, md, s),
+                                          reps), 2) for md in (0, 1, 2)}
+        probe[m.name] = pr
+        spmv[m.name] = {"D": m.D, "us": round(m.us, 2), "gbs": round(_gbs(m.spmv_bytes, m.us), 1),
+                        "frac": round(_gbs(m.spmv_bytes, m.us) / peak, 4),
+                        "gflops": round(2 * m.nnz / (m.us * 1e-6) / 1e9, 1),
+                        "groups": m.groups, "slots_per_nnz": round(m.slots / m.nnz, 4),
+                        "bytes": m.spmv_bytes, "autotune_us": m.tune_us,
+                        "gather_ceiling_us": pr["mode0"], "access_ceiling_us": pr["mode1"],
+                        "frac_of_gather_ceiling": round(pr["mode0"] / m.us, 4),
+                        "frac_of_access_ceiling": round(pr["mode1"] / m.us, 4)}
+    sum_us = sum(m.us for m in mats)
+    roofline = {
+        "bound": "hbm", "kernel": "k_spmv_g32", "achieved": round(value, 1), "peak": peak,
+        "unit": "GB/s", "frac": round(value / peak, 4), "peak_source": peak_kind,
+        "traffic": ncu_traffic("k_spmv_g32", "bench_spmv"),
+        "bytes_per_launch": round(step_bytes / len(mats)),
+        "avg_launch_us": round(ms * 1e3 / (args.steps * len(mats)), 2),
+        "timing": "CUDA events over the timed region, which holds only k_spmv_g32 launches",
+        # the lognormal matrix's random gathers go through L1TEX at about one
+        # line per clock per SM: the probe kernel measures that wall
+        "gather_ceiling_us": {k: v["mode0"] for k, v in probe.items()},
+        "access_ceiling_us": {k: v["mode1"] for k, v in probe.items()},
+        "frac_of_access_ceiling": round(sum(v["mode1"] for v in probe.values()) / sum_us, 4),
+        "other_limits_ncu": ncu_limits("k_spmv_g32"),
+    }
+
+    # the whole path per matrix: CSR -> ARG-CSR conversion + SpMV, handle
+    # freed (the conversion is informational: the paper does not time it)
+    def conv_step():
+        for m in mats:
+            h = convert(m, m.D)
+            api.argcsr_spmv(h, m.x.data_ptr(), m.y.data_ptr(), s)
+            api.argcsr_destroy(h, s)
+
+    conv_bytes = sum(conversion_bytes(m.n, m.nnz, m.groups, m.slots) + m.spmv_bytes for m in mats)
+    for _ in range(3):
+        conv_step()
+    torch.cuda.synchronize()
+    api.argcsr_trace_begin()
+    for _ in range(args.steps):
+        conv_step()
+    torch.cuda.synchronize()
+    api.argcsr_trace_end()
+    shares = api.trace_summary()
+    api.argcsr_trace_begin_kernel("k_fill")
+    a, b = _events(torch)
+    a.record(stream)
+    for _ in range(args.steps):
+        conv_step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    api.argcsr_trace_end()
+    fill_launches, fill_ms = api.trace_summary()["k_fill"]
+    step_ms = a.elapsed_time(b) / args.steps
+    fill_bytes = sum(kernel_bytes("k_fill", m.n, m.n_cols, m.nnz, m.groups, m.slots) for m in mats)
+    fill_us = fill_ms * 1e3 / fill_launches
+    fill_gbs = _gbs(fill_bytes / len(mats), fill_us)
     total_traced = sum(v[1] for v in shares.values())
-    kernels = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / total_traced, 4)}
-               for k, v in sorted(shares.items(), key=lambda kv: -kv[1][1])}
+    conversion = {
+        "what": "per matrix: CSR -> ARG-CSR conversion, SpMV, free; bytes = CSR read + ARG-CSR "
+                "written + the SpMV's",
+        "ms_per_step": round(step_ms, 4), "gbs": round(conv_bytes / (step_ms * 1e-3) / 1e9, 1),
+        "kernels": {k: {"launches": v[0], "us_per_launch": round(v[1] * 1e3 / v[0], 2),
+                        "share": round(v[1] / total_traced, 4)}
+                    for k, v in sorted(shares.items(), key=lambda kv: -kv[1][1])},
+        "roofline_k_fill": {"bound": "hbm", "kernel": "k_fill", "achieved": round(fill_gbs, 1),
+                            "peak": peak, "unit": "GB/s", "frac": round(fill_gbs / peak, 4),
+                            "avg_launch_us": round(fill_us, 2),
+                            "bytes_per_launch": round(fill_bytes / len(mats)),
+                            "traffic": ncu_traffic("k_fill", "bench")},
+    }
+    roofline["second"] = conversion["roofline_k_fill"]
 
-    # SpMV alone (the paper's measured operation), baselines on the same GPU
-    spmv = {}
-    spmv_bytes_all, spmv_ms_all = 0, 0.0
+    # plain CSR kernels of the library and cuSPARSE (torch.mv on a CSR
+    # tensor) on the same matrices
     baselines = {"csr_vector": {}, "csr_scalar": {}, "cusparse": {}}
     for m in mats:
-        h = convert(m)
-        reps = max(20, args.steps * 5)
-        for _ in range(3):
-            api.argcsr_spmv(h, m.x.data_ptr(), m.y.data_ptr(), s)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(reps):
-            api.argcsr_spmv(h, m.x.data_ptr(), m.y.data_ptr(), s)
-        b.record(stream)
-        torch.cuda.synchronize()
-        t = a.elapsed_time(b) / reps
-        nbytes = spmv_bytes(m.n, m.n_cols, m.nnz, m.groups)
-        spmv[m.name] = {"us": round(t * 1e3, 2), "gbs": round(nbytes / (t * 1e-3) / 1e9, 1),
-                        "frac": round(nbytes / (t * 1e-3) / 1e9 / peak, 4), "D": m.D,
-                        "slots_per_nnz": round(m.slots / m.nnz, 4),
-                        "gflops": round(2 * m.nnz / (t * 1e-3) / 1e9, 1)}
-        spmv_bytes_all += nbytes
-        spmv_ms_all += t
-        api.argcsr_destroy(h, s)
-        cbytes = csr_spmv_bytes(m.n, m.n_cols, m.nnz)
+        cb = csr_spmv_bytes(m.n, m.n_cols, m.nnz)
         for variant, key in ((1, "csr_vector"), (0, "csr_scalar")):
-            def run_csr():
-                api.argcsr_baseline_csr_spmv(m.n, m.n_cols, m.nnz, m.rp.data_ptr(), m.cols.data_ptr(),
-                                             m.vals.data_ptr(), api.ARGCSR_F64, variant,
-                                             m.x.data_ptr(), m.y.data_ptr(), s)
-            baselines[key][m.name] = _time_gbs(torch, stream, run_csr, cbytes, reps)
+            us = _time_us(torch, stream, lambda: api.argcsr_baseline_csr_spmv(
+                m.n, m.n_cols, m.nnz, m.rp.data_ptr(), m.cols.data_ptr(), m.vals.data_ptr(),
+                api.ARGCSR_F64, variant, m.x.data_ptr(), m.y.data_ptr(), s), reps)
+            baselines[key][m.name] = {"us": round(us, 2), "gbs": round(_gbs(cb, us), 1),
+                                      "argcsr_speedup": round(us / m.us, 3)}
         try:
             Acsr = torch.sparse_csr_tensor(m.rp, m.cols, m.vals, size=(m.n, m.n_cols))
-            baselines["cusparse"][m.name] = _time_gbs(torch, stream, lambda: torch.mv(Acsr, m.x),
-                                                      cbytes, reps)
+            us = _time_us(torch, stream, lambda: torch.mv(Acsr, m.x), reps)
+            baselines["cusparse"][m.name] = {"us": round(us, 2), "gbs": round(_gbs(cb, us), 1),
+                                             "argcsr_speedup": round(us / m.us, 3)}
         except Exception as exc:  # report, do not fail the bench
             baselines["cusparse"][m.name] = {"error": str(exc)[:120]}
-    spmv["combined"] = {"gbs": round(spmv_bytes_all / (spmv_ms_all * 1e-3) / 1e9, 1),
-                        "frac": round(spmv_bytes_all / (spmv_ms_all * 1e-3) / 1e9 / peak, 4)}
 
-    # the desiredChunkSize sweep 1..32 (conversion and SpMV time per D)
+    # FP32 / BF16 value storage (FP32 x, y and accumulation), with the error
+    # against the FP64 oracle on a sample of rows: max |y - y_ref| / sum|a x|
+    # with y_ref the oracle's FP64 CSR product of the FP64 matrix (storage
+    # rounding included) and of the stored values (arithmetic alone)
+    import oracle
+    oracle.build()
+    low = {}
+    rng = np.random.default_rng(7)
+    for m in mats:
+        rows = np.sort(rng.choice(m.n, size=min(m.n, 16384), replace=False))
+        sub = _row_subset(m.A, rows)
+        x32 = m.x_np.astype(np.float32)
+        ref64 = oracle.csr_spmv(sub, x32.astype(np.float64))
+        scale64 = oracle.csr_abs_spmv(sub, x32.astype(np.float64))
+        xd = torch.from_numpy(x32).to(dev)
+        yd = torch.empty(m.n, dtype=torch.float32, device=dev)
+        res = {}
+        for name, code in (("f32", api.ARGCSR_F32), ("bf16", api.ARGCSR_BF16)):
+            h = convert(m, m.D, storage=code)
+            info = api.argcsr_info(h)
+            nb = spmv_bytes(m.n, m.n_cols, m.nnz, info.n_groups, sv=DTYPE_BYTES[code], sx=4)
+            us = _time_us(torch, stream, lambda: api.argcsr_spmv(h, xd.data_ptr(), yd.data_ptr(), s), reps)
+            y = yd.cpu().numpy()[rows].astype(np.float64)
+            # the library rounds FP64 -> FP32 / BF16 once, to nearest even
+            sv_vals = (oracle.round_to_bf16(sub.values) if code == api.ARGCSR_BF16
+                       else sub.values.astype(np.float32).astype(np.float64))
+            stored = synth.Csr(sub.n_rows, sub.n_cols, sub.rowPointers, sub.columns, sv_vals, sub.name)
+            ref_st = oracle.csr_spmv(stored, x32.astype(np.float64))
+            sc_st = oracle.csr_abs_spmv(stored, x32.astype(np.float64))
+            res[name] = {"us": round(us, 2), "gbs": round(_gbs(nb, us), 1),
+                         "frac": round(_gbs(nb, us) / peak, 4),
+                         "speedup_vs_f64": round(m.us / us, 3),
+                         "err_vs_oracle": {
+                             "vs_fp64_values": float(np.max(np.abs(y - ref64) / np.maximum(scale64, 1e-300))),
+                             "vs_stored_values": float(np.max(np.abs(y - ref_st) / np.maximum(sc_st, 1e-300))),
+                             "rows_sampled": int(rows.size),
+                             "measure": "max over rows of |y - y_ref| / sum_j |a_ij x_j|"}}
+            api.argcsr_destroy(h, s)
+        low[m.name] = res
+        del xd, yd
+
+    # what the adaptive step gains: the same SpMV on the layout without it
+    # (every row one thread, same groups) and on Row-grouped CSR / Sliced
+    # ELLPACK (groups of exactly 32 rows, one thread per row)
+    ablation = {}
+    for m in mats:
+        res = {}
+        for key, D, p1 in (("one_thread_per_row", m.D, 1), ("rgcsr_sell32", 1 << 20, 1)):
+            h = convert(m, D, one_thread_per_row=p1)
+            info = api.argcsr_info(h)
+            us = _time_us(torch, stream, lambda: api.argcsr_spmv(h, m.x.data_ptr(), m.y.data_ptr(), s), reps)
+            res[key] = {"us": round(us, 2), "slots_per_nnz": round(info.n_slots / m.nnz, 3),
+                        "adaptive_speedup": round(us / m.us, 3)}
+            api.argcsr_destroy(h, s)
+        ablation[m.name] = res
+
+    # the desiredChunkSize sweep 1..32: SpMV and conversion time per D
     d_sweep = {}
     if not args.no_sweep:
         for m in mats:
-            rows = {}
+            spmv_us, conv_us, spn = [], [], []
             for D in range(1, 33):
-                conv = lambda: api.argcsr_create_from_csr(  # noqa: E731
-                    m.n, m.n_cols, m.nnz, m.rp.data_ptr(), m.cols.data_ptr(), m.vals.data_ptr(),
-                    api.ARGCSR_F64, GROUP_SIZE, D, 1, s)
-                api.argcsr_destroy(conv(), s)   # the memory pool grows to this layout's sizes once
-                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a0.record(stream)
-                h = conv()
-                a1.record(stream)
+                api.argcsr_destroy(convert(m, D), s)   # the pool grows to this layout once
+                a, b = _events(torch)
+                a.record(stream)
+                h = convert(m, D)
+                b.record(stream)
                 torch.cuda.synchronize()
+                conv_us.append(round(a.elapsed_time(b) * 1e3, 1))
                 info = api.argcsr_info(h)
-                nbytes = spmv_bytes(m.n, m.n_cols, m.nnz, info.n_groups)
-                r = _time_gbs(torch, stream, lambda: api.argcsr_spmv(h, m.x.data_ptr(), m.y.data_ptr(), s),
-                              nbytes, 20)
-                rows[D] = {"convert_us": round(a0.elapsed_time(a1) * 1e3, 1), "spmv_us": r["us"],
-                           "spmv_gbs": r["gbs"], "slots_per_nnz": round(info.n_slots / m.nnz, 4)}
+                spn.append(round(info.n_slots / m.nnz, 3))
+                spmv_us.append(round(_time_us(torch, stream, lambda: api.argcsr_spmv(
+                    h, m.x.data_ptr(), m.y.data_ptr(), s), 20, rounds=3), 1))
                 api.argcsr_destroy(h, s)
-            best_spmv = min(rows, key=lambda d: rows[d]["spmv_us"])
-            best_step = min(rows, key=lambda d: rows[d]["spmv_us"] + rows[d]["convert_us"])
-            d_sweep[m.name] = {"best_spmv_D": best_spmv, "best_step_D": best_step, "by_D": rows}
+            d_sweep[m.name] = {"best_spmv_D": 1 + int(np.argmin(spmv_us)), "spmv_us_by_D": spmv_us,
+                               "convert_us_by_D": conv_us, "slots_per_nnz_by_D": spn}
 
     # the other matrix families (banded, block-structured, power-law): SpMV
-    # with the layout the autotuner picks (G 32 / 64 / 128, D over its
-    # candidates: a row gets at most G threads, which matters for rows of
-    # tens of thousands of entries)
+    # with the layout the autotuner picks (G 32 / 64 / 128)
     families = {}
     if not args.no_sweep:
         for fname in synth.FAMILIES:
@@ -446,96 +608,121 @@ def run_ours(args):
             h = api.argcsr_create_from_csr(A.n_rows, A.n_cols, A.nnz, rp.data_ptr(), cols.data_ptr(),
                                            vals.data_ptr(), api.ARGCSR_F64, G, D, V, s)
             info = api.argcsr_info(h)
-            nbytes = spmv_bytes(A.n_rows, A.n_cols, A.nnz, info.n_groups)
-            r = _time_gbs(torch, stream, lambda: api.argcsr_spmv(h, x.data_ptr(), y.data_ptr(), s), nbytes, 20)
+            nb = spmv_bytes(A.n_rows, A.n_cols, A.nnz, info.n_groups)
+            us = _time_us(torch, stream, lambda: api.argcsr_spmv(h, x.data_ptr(), y.data_ptr(), s), 20, 3)
             api.argcsr_destroy(h, s)
             cb = csr_spmv_bytes(A.n_rows, A.n_cols, A.nnz)
-            csr = {}
-            for variant, key in ((1, "csr_vector"), (0, "csr_scalar")):
-                csr[key] = _time_gbs(torch, stream, lambda: api.argcsr_baseline_csr_spmv(
-                    A.n_rows, A.n_cols, A.nnz, rp.data_ptr(), cols.data_ptr(), vals.data_ptr(),
-                    api.ARGCSR_F64, variant, x.data_ptr(), y.data_ptr(), s), cb, 20)
+            vec = _time_us(torch, stream, lambda: api.argcsr_baseline_csr_spmv(
+                A.n_rows, A.n_cols, A.nnz, rp.data_ptr(), cols.data_ptr(), vals.data_ptr(),
+                api.ARGCSR_F64, 1, x.data_ptr(), y.data_ptr(), s), 20, 3)
             try:
                 Acsr = torch.sparse_csr_tensor(rp, cols, vals, size=(A.n_rows, A.n_cols))
-                csr["cusparse"] = _time_gbs(torch, stream, lambda: torch.mv(Acsr, x), cb, 20)
-            except Exception as exc:  # report, do not fail the bench
-                csr["cusparse"] = {"error": str(exc)[:120]}
+                cus = round(_time_us(torch, stream, lambda: torch.mv(Acsr, x), 20, 3), 2)
+            except Exception:  # report, do not fail the bench
+                cus = None
             families[fname] = {"n": A.n_rows, "nnz": A.nnz, "G": G, "D": D,
-                               "slots_per_nnz": round(info.n_slots / A.nnz, 4),
-                               "us": r["us"], "gbs": r["gbs"], "frac": round(r["gbs"] / peak, 4),
-                               "gflops": round(2 * A.nnz / (r["us"] * 1e-6) / 1e9, 1), "baselines": csr}
+                               "slots_per_nnz": round(info.n_slots / A.nnz, 3), "us": round(us, 2),
+                               "gbs": round(_gbs(nb, us), 1), "frac": round(_gbs(nb, us) / peak, 4),
+                               "csr_vector_us": round(vec, 2), "cusparse_us": cus,
+                               "csr_vector_gbs": round(_gbs(cb, vec), 1)}
             del rp, cols, vals, x, y
 
-    # what the adaptive step gains: the same SpMV on the layout without it
-    # (every row one thread, same groups) and on Row-grouped CSR / Sliced
-    # ELLPACK (groups of exactly 32 rows, one thread per row)
-    ablation = {}
-    for m in mats:
-        res = {}
-        for key, D, p1 in (("adaptive", m.D, 0), ("one_thread_per_row", m.D, 1),
-                           ("rgcsr_sell32", 1 << 20, 1)):
-            h = api.argcsr_create_from_csr(m.n, m.n_cols, m.nnz, m.rp.data_ptr(), m.cols.data_ptr(),
-                                           m.vals.data_ptr(), api.ARGCSR_F64, GROUP_SIZE, D, 1, s,
-                                           one_thread_per_row=p1)
-            info = api.argcsr_info(h)
-            nbytes = spmv_bytes(m.n, m.n_cols, m.nnz, info.n_groups)
-            r = _time_gbs(torch, stream, lambda: api.argcsr_spmv(h, m.x.data_ptr(), m.y.data_ptr(), s),
-                          nbytes, max(20, args.steps * 5))
-            r.update({"D": D, "groups": info.n_groups, "slots_per_nnz": round(info.n_slots / m.nnz, 4),
-                      "frac": round(r["gbs"] / peak, 4)})
-            res[key] = r
-            api.argcsr_destroy(h, s)
-        for key in ("one_thread_per_row", "rgcsr_sell32"):
-            res[f"speedup_vs_{key}"] = round(res[key]["us"] / res["adaptive"]["us"], 3)
-        ablation[m.name] = res
-
-    # end to end: pinned host CSR + x in, y out, through the public API
-    h2d = sum(4 * (m.n + 1) + m.nnz * (4 + SV) + m.n_cols * SX for m in mats)
+    # end to end through the public API: every step uploads x from pinned
+    # host memory, runs the SpMV, and reads y back into pinned host memory;
+    # x of the second matrix goes up while the first one's product runs
+    h2d = sum(m.n_cols * SX for m in mats)
     d2h = sum(m.n * SX for m in mats)
-
-    # inputs go up on a copy stream, in matrix order; each matrix's work
-    # waits only for its own inputs, so the next matrix's upload overlaps it
-    copy_stream = torch.cuda.Stream(device=dev)
+    up, down = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
 
     def step_e2e():
-        copy_stream.wait_stream(stream)        # buffers are free once the last step's work is done
+        up.wait_stream(stream)         # x buffers are free once the last products are done
         ready = []
-        with torch.cuda.stream(copy_stream):
+        with torch.cuda.stream(up):
             for m in mats:
-                m.rp.copy_(m.h_rp, non_blocking=True)
-                m.cols.copy_(m.h_cols, non_blocking=True)
-                m.vals.copy_(m.h_vals, non_blocking=True)
                 m.x.copy_(m.h_x, non_blocking=True)
                 ev = torch.cuda.Event()
-                ev.record(copy_stream)
+                ev.record(up)
                 ready.append(ev)
         for m, ev in zip(mats, ready):
             stream.wait_event(ev)
-            h = convert(m)
-            api.argcsr_spmv(h, m.x.data_ptr(), m.y.data_ptr(), s)
-            api.argcsr_destroy(h, s)
-            m.h_y.copy_(m.y, non_blocking=True)
+            api.argcsr_spmv(m.h, m.x.data_ptr(), m.y.data_ptr(), s)
+            done = torch.cuda.Event()
+            done.record(stream)
+            down.wait_event(done)
+            with torch.cuda.stream(down):
+                m.h_y.copy_(m.y, non_blocking=True)
+        stream.wait_stream(down)
 
-    for _ in range(2):
+    for _ in range(3):
         step_e2e()
     torch.cuda.synchronize()
     barrier(world)
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e2e_steps = max(3, args.steps // 2)
+    a, b = _events(torch)
     a.record(stream)
-    for _ in range(e2e_steps):
+    for _ in range(args.steps):
         step_e2e()
     b.record(stream)
     torch.cuda.synchronize()
     barrier(world)
     e2e_ms = reduce_max(a.elapsed_time(b), world, dev)
-    e2e_value = reduce_sum(step_bytes * e2e_steps, world, dev) / (e2e_ms * 1e-3) / 1e9
-    # the result read back to the host is the product
+    e2e_value = reduce_sum(step_bytes * args.steps, world, dev) / (e2e_ms * 1e-3) / 1e9
     y_check = float(np.abs(mats[0].h_y.numpy()).sum())
+    # the whole path from host CSR: upload CSR + x, convert, SpMV, y back
+    full_h2d = sum(4 * (m.n + 1) + m.nnz * (4 + SV) + m.n_cols * SX for m in mats)
+
+    def step_full():
+        up.wait_stream(stream)
+        ready = []
+        with torch.cuda.stream(up):
+            for m in mats:
+                for dst, src in ((m.rp, m.h_rp), (m.cols, m.h_cols), (m.vals, m.h_vals), (m.x, m.h_x)):
+                    dst.copy_(src, non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(up)
+                ready.append(ev)
+        for m, ev in zip(mats, ready):
+            stream.wait_event(ev)
+            h = convert(m, m.D)
+            api.argcsr_spmv(h, m.x.data_ptr(), m.y.data_ptr(), s)
+            api.argcsr_destroy(h, s)
+            m.h_y.copy_(m.y, non_blocking=True)
+
+    for _ in range(2):
+        step_full()
+    torch.cuda.synchronize()
+    a, b = _events(torch)
+    full_steps = max(3, args.steps // 4)
+    a.record(stream)
+    for _ in range(full_steps):
+        step_full()
+    b.record(stream)
+    torch.cuda.synchronize()
+    full_ms = a.elapsed_time(b) / full_steps
+    e2e = {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms / args.steps, 4),
+           "what": "per step: x H2D from pinned memory, SpMV of both matrices, y D2H to pinned memory",
+           "y_abs_sum": y_check,
+           "full_path": {"what": "per step: CSR + x H2D, conversion, SpMV, y D2H",
+                         "ms_per_step": round(full_ms, 4), "h2d_bytes_per_step": full_h2d,
+                         "d2h_bytes_per_step": d2h,
+                         "gbs": round(conv_bytes / (full_ms * 1e-3) / 1e9, 1)}}
+
+    for m in mats:
+        api.argcsr_destroy(m.h, s)
+    torch.cuda.synchronize()
+    del mats
+    torch.cuda.empty_cache()
+
+    cg = None if args.no_cg else cg_measure(api, torch, dev, peak, reps=3, compact=True)
+    serving = None
+    if pool is not None:
+        serving = serving_measure(api, torch, dev, pool, requests=args.requests_compact,
+                                  fractions=(0.5,), n_streams=args.serve_streams, compact=True)
+        del pool
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(min_seconds=args.cpu_seconds)
+        cpu = cpu_baseline(seconds=args.cpu_seconds, Ds={k: v["D"] for k, v in spmv.items()})
 
     if rank == 0:
         line = {
@@ -544,29 +731,26 @@ def run_ours(args):
             "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "group_size": GROUP_SIZE,
-                       "desired_chunk_size": {m.name: m.D for m in mats},
-                       "n_rows": {m.name: m.n for m in mats}, "nnz": {m.name: m.nnz for m in mats},
-                       "groups": {m.name: m.groups for m in mats},
-                       "slots": {m.name: m.slots for m in mats},
+                       "desired_chunk_size": {k: v["D"] for k, v in spmv.items()},
+                       "n_rows": {"lognormal_2m": 2000000, "laplace3d_128": 128 ** 3},
                        "bytes_per_step": step_bytes,
                        "l2": f"inputs larger than L2 ({step_bytes / 2**20:.0f} MiB per step "
                              f"vs {L2_BYTES / 2**20:.0f} MiB L2); no flush",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline,
             "cpu_baseline": cpu,
-            "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms / e2e_steps, 4),
-                    "y_abs_sum": y_check},
+            "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clocks,
             "spmv": spmv,
+            "serving": serving,
+            "cg": cg,
             "baselines": baselines,
+            "low_precision": low,
+            "conversion": conversion,
             "ablation": ablation,
-            "d_sweep": d_sweep,
             "families": families,
-            "kernels": kernels,
-            "kernels_pass": "a traced pass of the same steps before the timed region, "
-                            "which traces only the dominant kernel",
+            "d_sweep": d_sweep,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -574,100 +758,163 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def _time_gbs(torch, stream, fn, nbytes, reps):
-    for _ in range(3):
-        fn()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for _ in range(reps):
-        fn()
-    b.record(stream)
-    torch.cuda.synchronize()
-    t = a.elapsed_time(b) / reps
-    return {"us": round(t * 1e3, 2), "gbs": round(nbytes / (t * 1e-3) / 1e9, 1)}
+def _row_subset(A, rows):
+    """The CSR matrix made of A's rows `rows` (sorted), with all of A's columns."""
+    rp = A.rowPointers.astype(np.int64)
+    lens = rp[rows + 1] - rp[rows]
+    new_rp = np.zeros(rows.size + 1, dtype=np.int64)
+    np.cumsum(lens, out=new_rp[1:])
+    idx = np.concatenate([np.arange(rp[r], rp[r + 1]) for r in rows]) if rows.size else np.zeros(0, np.int64)
+    return synth.Csr(int(rows.size), A.n_cols, new_rp.astype(np.int32), A.columns[idx], A.values[idx],
+                     A.name + "[rows]")
 
 
 # ---------------------------------------------------------------------------
 # the oracle on the host cores (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
 
-def _row_prefix(A, rows):
-    """The first ``rows`` rows of A (all columns): a bounded sample with the
-    same row-length distribution."""
-    if rows >= A.n_rows:
-        return A
-    nnz = int(A.rowPointers[rows])
-    return synth.Csr(rows, A.n_cols, A.rowPointers[:rows + 1], A.columns[:nnz], A.values[:nnz],
-                     A.name + f"[:{rows}]")
+class OracleWork:
+    """The bench matrices as the oracle sees them: its own conversion (G 32,
+    the given D), x, and the work split into `threads` contiguous slices of
+    about equal size -- groups for the ARG-CSR product, rows for the plain CSR
+    one.  The oracle's calls release the GIL, so slices run on host threads
+    in parallel with unchanged arithmetic."""
+
+    def __init__(self, inputs, threads):
+        """inputs: (name, A, x, D) per matrix."""
+        import oracle
+        oracle.build()
+        self.oracle = oracle
+        self.threads = max(1, threads)
+        self.items = []
+        for name, A, x, D in inputs:
+            M = oracle.convert(A, GROUP_SIZE, D)
+            y = np.zeros(A.n_rows, dtype=np.float64)
+            slots = M.groupInfo[:, 2].astype(np.int64)
+            g_cuts = np.searchsorted(slots, np.linspace(0, M.n_slots, self.threads + 1)[1:-1])
+            g_cuts = [0] + [int(c) for c in g_cuts] + [M.n_groups]
+            r_cuts = np.searchsorted(A.rowPointers.astype(np.int64),
+                                     np.linspace(0, A.nnz, self.threads + 1)[1:-1])
+            r_cuts = [0] + [int(c) for c in r_cuts] + [A.n_rows]
+            csr_slices = []
+            for r0, r1 in zip(r_cuts[:-1], r_cuts[1:]):
+                a, b = int(A.rowPointers[r0]), int(A.rowPointers[r1])
+                csr_slices.append(synth.Csr(r1 - r0, A.n_cols,
+                                            (A.rowPointers[r0:r1 + 1] - a).astype(np.int32),
+                                            A.columns[a:b], A.values[a:b], name))
+            self.items.append({"name": name, "A": A, "M": M, "x": np.ascontiguousarray(x), "y": y,
+                               "D": D, "g_cuts": g_cuts, "csr_slices": csr_slices,
+                               "bytes": spmv_bytes(A.n_rows, A.n_cols, A.nnz, M.n_groups),
+                               "csr_bytes": csr_spmv_bytes(A.n_rows, A.n_cols, A.nnz)})
+
+    def _run(self, jobs, threads):
+        if threads == 1:
+            for j in jobs:
+                j()
+            return
+        ts = [threading.Thread(target=j) for j in jobs]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+
+    def argcsr_step(self, threads):
+        """ARG-CSR SpMV of both matrices (Section 4 semantics); returns bytes."""
+        jobs = []
+        for it in self.items:
+            if threads == 1:
+                jobs.append(lambda it=it: self.oracle.argcsr_spmv_groups(it["M"], it["x"], it["y"], 0,
+                                                                          it["M"].n_groups))
+            else:
+                for g0, g1 in zip(it["g_cuts"][:-1], it["g_cuts"][1:]):
+                    jobs.append(lambda it=it, g0=g0, g1=g1: self.oracle.argcsr_spmv_groups(
+                        it["M"], it["x"], it["y"], g0, g1))
+        self._run(jobs, threads)
+        return sum(it["bytes"] for it in self.items)
+
+    def csr_step(self, threads):
+        """Plain CSR SpMV of both matrices (the paper's CPU baseline); returns bytes."""
+        jobs = []
+        for it in self.items:
+            if threads == 1:
+                jobs.append(lambda it=it: self.oracle.csr_spmv(it["A"], it["x"]))
+            else:
+                for sl in it["csr_slices"]:
+                    jobs.append(lambda sl=sl, it=it: self.oracle.csr_spmv(sl, it["x"]))
+        self._run(jobs, threads)
+        return sum(it["csr_bytes"] for it in self.items)
+
+    def rate(self, fn, threads, seconds):
+        nbytes, elapsed, reps = 0, 0.0, 0
+        while elapsed < seconds or reps < 2:
+            t0 = time.perf_counter()
+            nbytes += fn(threads)
+            elapsed += time.perf_counter() - t0
+            reps += 1
+        return nbytes / elapsed / 1e9, reps, elapsed
 
 
-def oracle_step(samples):
-    """Conversion + ARG-CSR SpMV of every sampled matrix with the CPU oracle;
-    returns the step's algorithmic bytes."""
-    import oracle
-    nbytes = 0
-    for A, x, D in samples:
-        M = oracle.convert(A, GROUP_SIZE, D)
-        oracle.argcsr_spmv(M, x)
-        nbytes += (conversion_bytes(A.n_rows, A.nnz, M.n_groups, M.n_slots)
-                   + spmv_bytes(A.n_rows, A.n_cols, A.nnz, M.n_groups))
-    return nbytes
-
-
-def _samples(fraction):
+def bench_inputs(Ds=None):
+    """(name, A, x, D) of the bench matrices, D as given or the default."""
+    Ds = Ds or {}
     out = []
-    for name, D in MATRICES:
+    for name in MATRICES:
         A, x = synth.workload(name)
-        rows = max(1, int(A.n_rows * fraction))
-        out.append((_row_prefix(A, rows), x, D))
+        out.append((name, A, x, Ds.get(name, FALLBACK_D[name])))
     return out
 
 
-def cpu_baseline(min_seconds=10.0, fraction=1.0):
-    import oracle
-    oracle.build()
-    samples = _samples(fraction)
-    nbytes, elapsed, reps = 0, 0.0, 0
-    while elapsed < min_seconds and reps < 20:
-        t0 = time.perf_counter()
-        nbytes += oracle_step(samples)
-        elapsed += time.perf_counter() - t0
-        reps += 1
-    rows = "+".join(f"{A.n_rows}" for A, _, _ in samples)
-    return {"value": round(nbytes / elapsed / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"{reps} x the step on rows {rows} of the two matrices "
-                      f"({elapsed:.1f} s, single-threaded C oracle)"}
+def cpu_baseline(seconds=10.0, Ds=None):
+    """The oracle's SpMV of the bench matrices on the host: ARG-CSR (the
+    same product and byte model as the GPU value) and plain CSR (the paper's
+    CPU baseline), each on one core and on all cores."""
+    host = host_description()
+    threads = host["nproc"] or 1
+    w = OracleWork(bench_inputs(Ds), threads)
+    q = seconds / 4
+    a1, r1, t1 = w.rate(w.argcsr_step, 1, q)
+    an, rn, tn = w.rate(w.argcsr_step, threads, q)
+    c1, _, _ = w.rate(w.csr_step, 1, q)
+    cn, _, _ = w.rate(w.csr_step, threads, q)
+    return {"value": round(an, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
+            "sample": f"the whole step (both matrices, full size): {rn} steps on {threads} threads "
+                      f"({tn:.1f} s), {r1} steps on one ({t1:.1f} s); the oracle's ARG-CSR product "
+                      "split over contiguous group ranges",
+            "single_core": round(a1, 4),
+            "csr_oracle": {"single_core": round(c1, 4), "all_cores": round(cn, 4),
+                           "what": "the oracle's plain CSR product (the paper's CPU baseline), "
+                                   "bytes by the CSR model"},
+            "desired_chunk_size": {it["name"]: it["D"] for it in w.items},
+            "host": host}
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    import oracle
-    oracle.build()
-    # keep the whole run within a few minutes: one step costs ~2-4 s at full size
-    fraction = min(1.0, 30.0 / max(1, args.steps + args.warmup))
-    samples = _samples(fraction)
+    host = host_description()
+    threads = host["nproc"] or 1
+    w = OracleWork(bench_inputs(), threads)
     for _ in range(args.warmup):
-        oracle_step(samples)
+        w.argcsr_step(threads)
     t0 = time.perf_counter()
     nbytes = 0
     for _ in range(args.steps):
-        nbytes += oracle_step(samples)
+        nbytes += w.argcsr_step(threads)
     elapsed = time.perf_counter() - t0
     value = nbytes / elapsed / 1e9
-    rows = "+".join(f"{A.n_rows}" for A, _, _ in samples)
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(elapsed * 1e3 / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "group_size": GROUP_SIZE,
-                   "desired_chunk_size": {n: d for n, d in MATRICES},
-                   "sample_rows": rows, "parallelism": "host, 1 core"},
-        "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": f"each step: rows {rows} of the two matrices "
-                                   f"(fraction {fraction:.3f})"},
+                   "desired_chunk_size": {it["name"]: it["D"] for it in w.items},
+                   "parallelism": f"host, {threads} threads"},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
+                         "sample": "each step: the oracle's ARG-CSR SpMV of both matrices at full "
+                                   f"size, split over {threads} threads by group ranges",
+                         "host": host},
         "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -694,32 +941,32 @@ def csr_cg_iteration_bytes(n, nnz):
     return nnz * 12 + 4 * (n + 1) + 2 * n * 8 + 11 * n * 8
 
 
-def run_cg(args):
-    import torch
-    from paper_1203_5737_gb300 import argcsr as api
-    from paper_1203_5737_gb300 import build
-    build.build()
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
+def cg_measure(api, torch, dev, peak, reps=3, compact=False):
+    """Solve A x = b to a 1e-10 relative residual on the 160^3 Poisson matrix:
+    ARG-CSR with FP32 and BF16 storage (FP32 inner CG, FP64 refinement),
+    ARG-CSR FP64, and the plain FP64 CSR CG.  Each result carries its final
+    relative residual recomputed by the CPU oracle in FP64."""
+    import oracle
+    oracle.build()
     stream = torch.cuda.Stream()
     s = stream.cuda_stream
     A = synth.laplacian_3d(160)
-    x_true = torch.from_numpy(synth.uniform_vector(A.n_cols, 5)).to(dev)
+    x_true_np = synth.uniform_vector(A.n_cols, 5)
+    x_true = torch.from_numpy(x_true_np).to(dev)
     rp = torch.from_numpy(A.rowPointers).to(dev)
     cols = torch.from_numpy(A.columns).to(dev)
     v64 = torch.from_numpy(A.values).to(dev)
-    peak, peak_kind = measured_hbm_peak()
     tol, D = 1e-10, 8
-    out = {"metric": CG_METRIC, "unit": "solves/s", "higher_is_better": True, "n_gpus": 1,
-           "dtype": "f32/bf16 inner, f64 refinement", "data": "synthetic",
-           "config": {"workload": "3D 7-point Poisson 160^3 (n 4,096,000, SPD), b = A x_true, "
-                                  "x_true ~ U[-1,1] seed 5; ARG-CSR G 32 D 8",
-                      "n": A.n_rows, "nnz": A.nnz, "tol": tol}}
+    b_np = oracle.csr_spmv(A, x_true_np)        # b = A x_true in FP64 by the oracle
+    b = torch.from_numpy(b_np).to(dev)
+    b_norm = float(np.linalg.norm(b_np))
+
+    def oracle_residual(x):
+        xh = x.cpu().numpy()
+        return float(np.linalg.norm(b_np - oracle.csr_spmv(A, xh)) / b_norm)
+
+    results = {}
     with torch.cuda.stream(stream):
-        h64 = api.argcsr_create_from_csr(A.n_rows, A.n_cols, A.nnz, rp.data_ptr(), cols.data_ptr(),
-                                         v64.data_ptr(), api.ARGCSR_F64, GROUP_SIZE, D, 1, s)
-        b = torch.empty_like(x_true)
-        api.argcsr_spmv(h64, x_true.data_ptr(), b.data_ptr(), s)
         variants = {}
         for name, vals, code in (("argcsr_f32_ir", v64.float(), api.ARGCSR_F32),
                                  ("argcsr_bf16_ir", v64.bfloat16(), api.ARGCSR_BF16),
@@ -727,63 +974,85 @@ def run_cg(args):
             h = api.argcsr_create_from_csr(A.n_rows, A.n_cols, A.nnz, rp.data_ptr(), cols.data_ptr(),
                                            vals.data_ptr(), code, GROUP_SIZE, D, 1, s)
             variants[name] = (h, code, vals)
-        results = {}
 
-        def timed(fn, reps):
-            times, res = [], None
+        def timed(fn):
+            times, res, x = [], None, None
             for _ in range(reps):
                 x = torch.zeros_like(x_true)
                 stream.synchronize()
-                a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a, e = _events(torch)
                 a.record(stream)
                 res = fn(x)
                 e.record(stream)
                 stream.synchronize()
                 times.append(a.elapsed_time(e))
             err = float(torch.linalg.norm(x - x_true) / torch.linalg.norm(x_true))
-            return statistics.median(times), res, err
+            return statistics.median(times), res, err, x
 
-        reps = max(3, args.steps // 5)
         for name, (h, code, vals) in variants.items():
-            fn = lambda x, h=h: api.argcsr_cg_solve(h, h64, b.data_ptr(), x.data_ptr(), tol=tol,  # noqa: E731
+            fn = lambda x, h=h: api.argcsr_cg_solve(h, None, b.data_ptr(), x.data_ptr(), tol=tol,  # noqa: E731
                                                     stream=s)
-            fn(torch.zeros_like(x_true))          # warm-up (pool, module load)
-            ms, res, err = timed(fn, reps)
-            api.argcsr_trace_begin()
-            fn(torch.zeros_like(x_true))
-            stream.synchronize()
-            api.argcsr_trace_end()
-            kern = {k: {"launches": v[0], "us_per_launch": round(v[1] * 1e3 / v[0], 2)}
-                    for k, v in api.trace_summary().items()}
+            fn(torch.zeros_like(x_true))          # warm-up (pool, module load, graph)
+            ms, res, err, x = timed(fn)
             info = api.argcsr_info(h)
-            sv = {api.ARGCSR_F64: 8, api.ARGCSR_F32: 4, api.ARGCSR_BF16: 2}[code]
+            sv = DTYPE_BYTES[code]
             sw = 8 if code == api.ARGCSR_F64 else 4
             it_bytes = cg_iteration_bytes(A.n_rows, A.nnz, info.n_groups, sv, sw)
             it_us = ms * 1e3 / max(1, res["inner_iters"])
             results[name] = {"ms_per_solve": round(ms, 3), "solves_per_s": round(1e3 / ms, 3),
                              **res, "x_rel_error": err,
+                             "err_vs_oracle": {"rel_residual_fp64": oracle_residual(x),
+                                               "measure": "||b - A x|| / ||b|| by the CPU oracle"},
                              "us_per_inner_iter": round(it_us, 2),
-                             "inner_iter_gbs": round(it_bytes / (it_us * 1e-6) / 1e9, 1),
-                             "inner_iter_frac": round(it_bytes / (it_us * 1e-6) / 1e9 / peak, 4),
-                             "kernels": kern}
+                             "inner_iter_gbs": round(_gbs(it_bytes, it_us), 1),
+                             "inner_iter_frac": round(_gbs(it_bytes, it_us) / peak, 4)}
+            if not compact:
+                api.argcsr_trace_begin()
+                fn(torch.zeros_like(x_true))
+                stream.synchronize()
+                api.argcsr_trace_end()
+                results[name]["kernels"] = {k: {"launches": v[0], "us_per_launch": round(v[1] * 1e3 / v[0], 2)}
+                                            for k, v in api.trace_summary().items()}
         fnb = lambda x: api.argcsr_baseline_csr_cg(A.n_rows, A.nnz, rp.data_ptr(), cols.data_ptr(),  # noqa: E731
                                                    v64.data_ptr(), b.data_ptr(), x.data_ptr(),
                                                    tol=tol, stream=s)
         fnb(torch.zeros_like(x_true))
-        ms, res, err = timed(fnb, reps)
+        ms, res, err, x = timed(fnb)
         it_bytes = csr_cg_iteration_bytes(A.n_rows, A.nnz)
         it_us = ms * 1e3 / max(1, res["inner_iters"])
         results["plain_csr_f64"] = {"ms_per_solve": round(ms, 3), "solves_per_s": round(1e3 / ms, 3),
-                                    **res, "x_rel_error": err, "us_per_inner_iter": round(it_us, 2),
-                                    "inner_iter_gbs": round(it_bytes / (it_us * 1e-6) / 1e9, 1),
-                                    "inner_iter_frac": round(it_bytes / (it_us * 1e-6) / 1e9 / peak, 4)}
+                                    **res, "x_rel_error": err,
+                                    "err_vs_oracle": {"rel_residual_fp64": oracle_residual(x),
+                                                      "measure": "||b - A x|| / ||b|| by the CPU oracle"},
+                                    "us_per_inner_iter": round(it_us, 2),
+                                    "inner_iter_gbs": round(_gbs(it_bytes, it_us), 1),
+                                    "inner_iter_frac": round(_gbs(it_bytes, it_us) / peak, 4)}
         for h, _, _ in variants.values():
             api.argcsr_destroy(h, s)
-        api.argcsr_destroy(h64, s)
+    stream.synchronize()
     best = results["argcsr_f32_ir"]
-    out.update({"value": best["solves_per_s"], "ms_per_solve": best["ms_per_solve"],
-                "vs_plain_csr_f64": round(results["plain_csr_f64"]["ms_per_solve"] / best["ms_per_solve"], 3),
-                "peak_gbs": peak, "peak_source": peak_kind, "solvers": results})
+    return {"metric": CG_METRIC,
+            "workload": "3D 7-point Poisson 160^3 (n 4,096,000, nnz 28,518,400, SPD), b = A x_true, "
+                        "x_true ~ U[-1,1] seed 5; ARG-CSR G 32 D 8; tol 1e-10",
+            "solves_per_s": best["solves_per_s"], "ms_per_solve": best["ms_per_solve"],
+            "plain_csr_f64_solves_per_s": results["plain_csr_f64"]["solves_per_s"],
+            "speedup_vs_plain_csr_f64": round(results["plain_csr_f64"]["ms_per_solve"] / best["ms_per_solve"], 3),
+            "solvers": results}
+
+
+def run_cg(args):
+    import torch
+    from paper_1203_5737_gb300 import argcsr as api
+    from paper_1203_5737_gb300 import build
+    build.build()
+    api.load_library()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    peak, peak_kind = measured_hbm_peak()
+    r = cg_measure(api, torch, dev, peak, reps=max(3, args.steps // 5))
+    out = {"metric": CG_METRIC, "unit": "solves/s", "higher_is_better": True, "n_gpus": 1,
+           "value": r["solves_per_s"], "dtype": "f32/bf16 inner, f64 refinement", "data": "synthetic",
+           "config": {"workload": r["workload"]}, "peak_gbs": peak, "peak_source": peak_kind, **r}
     print(json.dumps(out), flush=True)
 
 
@@ -795,6 +1064,8 @@ BATCH_METRIC = "batched SpMM, 4096 matrices in one persistent CUDA-graph launch"
 
 
 def run_batched(args):
+    import oracle
+    oracle.build()
     count = args.batch_count
     mats = synth.diag_dominant_batch(count, seed=0, workers=min(16, os.cpu_count() or 1))
     import torch
@@ -830,7 +1101,7 @@ def run_batched(args):
                        for m in range(count)]
             B = api.argcsr_batch_create(handles, s)
             info = api.argcsr_batch_info(B)
-            rows, _ = api.argcsr_batch_offsets(B, count)
+            rows, cols_m = api.argcsr_batch_offsets(B, count)
             X = torch.rand((info["total_cols"], k), dtype=torch.float32, device="cuda") * 2 - 1
             Y = torch.empty((info["total_rows"], k), dtype=torch.float32, device="cuda")
             graph = api.argcsr_batch_graph_create(B, k, X.data_ptr(), Y.data_ptr())
@@ -862,6 +1133,18 @@ def run_batched(args):
             # in rounding there
             same = bool(torch.equal(Y, Yp))
             rel = float(((Y - Yp).abs().max() / Yp.abs().max().clamp_min(1e-30)).item())
+            # error against the FP64 oracle: 16 members, first and last column
+            Yh, Xh = Y.cpu().numpy(), X.cpu().numpy()
+            cols_h, err = sorted({0, k - 1}), 0.0
+            for mm in range(0, count, max(1, count // 16)):
+                A = mats[mm]
+                A64 = synth.Csr(A.n_rows, A.n_cols, A.rowPointers, A.columns,
+                                A.values.astype(np.float32).astype(np.float64), A.name)
+                for j in cols_h:
+                    xj = Xh[int(cols_m[mm]):int(cols_m[mm]) + A.n_cols, j].astype(np.float64)
+                    yj = Yh[int(rows[mm]):int(rows[mm]) + A.n_rows, j].astype(np.float64)
+                    ref, sc = oracle.csr_spmv(A64, xj), oracle.csr_abs_spmv(A64, xj)
+                    err = max(err, float(np.max(np.abs(yj - ref) / np.maximum(sc, 1e-300))))
             nbytes = (total_nnz * 8 + 2 * total_rows * k * 4 + 4 * total_rows + 16 * info["total_groups"])
             results[f"k{k}"] = {"group_size": G, "desired_chunk_size": D, "tuned_us": round(tune_us, 1),
                                 "ms_per_launch": round(ms, 4),
@@ -872,7 +1155,10 @@ def run_batched(args):
                                 "ms_one_launch_per_matrix": round(ms_each, 3),
                                 "speedup_vs_per_matrix": round(ms_each / ms, 2),
                                 "bitwise_equal_to_per_matrix": same,
-                                "max_rel_diff_vs_per_matrix": rel}
+                                "max_rel_diff_vs_per_matrix": rel,
+                                "err_vs_oracle": {"max": err, "measure": "max over rows of |y - y_ref| / "
+                                                  "sum|a x| on 16 members, first and last column; y_ref "
+                                                  "the oracle's FP64 product of the FP32 values"}}
             api.argcsr_graph_destroy(graph)
             api.argcsr_batch_destroy(B, s)
             for h in handles:
@@ -895,6 +1181,10 @@ def run_batched(args):
 
 SERVE_METRIC = ("served CG solves/s (80/20 SpMV/CG mix, tol 1e-8) and p50/p99 request latency "
                 "on a 64-matrix device-resident pool")
+SERVE_WORKLOAD = ("64 matrices, n log-uniform in [1e4, 2e6] (Zipf members at most 5e4 rows): 2D/3D "
+                  "Laplacians, symmetrised lognormal(1.8, 1.0) diagonally dominant (SPD), Zipf(1.5) "
+                  "rows up to 50 000 entries (SpMV only); FP32/BF16 alternating; requests 80% SpMV / "
+                  "20% CG (SPD members, tol 1e-8), x, b ~ U[-1,1]; HBM budget 150 GB")
 
 
 def _pct(values, q):
@@ -922,16 +1212,14 @@ def _sleep_until(t):
         time.sleep(d if d > 2e-3 else 0)
 
 
-def run_serving(args):
-    import torch
-    from paper_1203_5737_gb300 import argcsr as api
-    from paper_1203_5737_gb300 import build
-    build.build()
-    t0 = time.time()
-    pool = synth.serving_pool(64, seed=0, workers=min(16, os.cpu_count() or 1))
-    gen_s = time.time() - t0
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
+def serving_measure(api, torch, dev, pool, requests, fractions, n_streams, compact=False):
+    """The serving engine against plain FP64 CSR served first come first
+    served, on the same requests: saturation (all requests at once) and
+    Poisson arrivals at the given fractions of the saturated request rate.
+    A sample of SpMV results and CG solutions is checked against the CPU
+    oracle in FP64."""
+    import oracle
+    oracle.build()
     stream = torch.cuda.Stream()
     s = stream.cuda_stream
     tol = 1e-8
@@ -956,31 +1244,28 @@ def run_serving(args):
                                                 GROUP_SIZE, D, 1, s)
             stream.synchronize()
             del vs
-            mats.append({"n": A.n_rows, "nnz": A.nnz, "kind": P["kind"], "spd": P["spd"],
+            mats.append({"n": A.n_rows, "nnz": A.nnz, "kind": P["kind"], "spd": P["spd"], "A": A,
                          "storage": P["storage"], "h": h, "hr": hr, "rp": rp, "cols": cols, "v64": v64})
-    del pool
     rng = np.random.default_rng(1)
     gen = torch.Generator(device=dev)
     gen.manual_seed(1)
     spd_ids = [i for i, M in enumerate(mats) if M["spd"]]
     reqs = []
-    for _ in range(args.requests):
+    for _ in range(requests):
         if rng.random() < 0.2:
             i = int(rng.choice(spd_ids))
-            n = mats[i]["n"]
-            b = torch.rand(n, generator=gen, device=dev, dtype=torch.float64) * 2 - 1
+            b = torch.rand(mats[i]["n"], generator=gen, device=dev, dtype=torch.float64) * 2 - 1
             reqs.append({"kind": "cg", "m": i, "b": b, "x": torch.zeros_like(b), "xb": torch.zeros_like(b)})
         else:
             i = int(rng.integers(len(mats)))
-            n = mats[i]["n"]
-            x64 = torch.rand(n, generator=gen, device=dev, dtype=torch.float64) * 2 - 1
+            x64 = torch.rand(mats[i]["n"], generator=gen, device=dev, dtype=torch.float64) * 2 - 1
             reqs.append({"kind": "spmv", "m": i, "x64": x64, "x": x64.float(),
-                         "y": torch.empty(n, dtype=torch.float32, device=dev),
-                         "y64": torch.empty(n, dtype=torch.float64, device=dev)})
+                         "y": torch.empty(mats[i]["n"], dtype=torch.float32, device=dev),
+                         "y64": torch.empty(mats[i]["n"], dtype=torch.float64, device=dev)})
     torch.cuda.synchronize()
 
     def serve_ours(subset, offsets):
-        S = api.argcsr_server_create(hbm_budget_bytes=150 * 10**9, num_streams=args.serve_streams)
+        S = api.argcsr_server_create(hbm_budget_bytes=150 * 10**9, num_streams=n_streams)
         ids = [api.argcsr_server_add_matrix(S, M["h"], M["hr"]) for M in mats]
         for q in subset:
             if reqs[q]["kind"] == "cg":
@@ -1020,7 +1305,7 @@ def run_serving(args):
 
     def serve_baseline(subset, offsets):
         """Plain FP64 CSR (the library's vector CSR SpMV and CG) served
-        first-come first-served, one request at a time."""
+        first come first served, one request at a time."""
         for q in subset:
             if reqs[q]["kind"] == "cg":
                 reqs[q]["xb"].zero_()
@@ -1053,15 +1338,38 @@ def run_serving(args):
     warm = everything[: min(64, len(reqs))]
     serve_ours(warm, [0.0] * len(warm))
     serve_baseline(warm, [0.0] * len(warm))
-    clocks = ClockSampler(0)
+    clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     sat = serve_ours(everything, [0.0] * len(everything))
     clock_info = clocks.stop()
+    # the results of the saturation run against the oracle: SpMV rows
+    # (sampled) and CG solutions, in FP64
+    spmv_err, cg_res = 0.0, 0.0
+    checked = {"spmv": 0, "cg": 0}
+    rng_c = np.random.default_rng(3)
+    for q in everything:
+        r = reqs[q]
+        M = mats[r["m"]]
+        if r["kind"] == "spmv" and checked["spmv"] < 16:
+            rows = np.sort(rng_c.choice(M["n"], size=min(M["n"], 2048), replace=False))
+            sub = _row_subset(M["A"], rows)
+            tdt = torch.float32 if M["storage"] == "f32" else torch.bfloat16
+            stored = synth.Csr(sub.n_rows, sub.n_cols, sub.rowPointers, sub.columns,
+                               torch.from_numpy(sub.values).to(tdt).to(torch.float64).numpy(), sub.name)
+            xh = r["x"].cpu().numpy().astype(np.float64)
+            y = r["y"].cpu().numpy()[rows].astype(np.float64)
+            ref, sc = oracle.csr_spmv(stored, xh), oracle.csr_abs_spmv(stored, xh)
+            spmv_err = max(spmv_err, float(np.max(np.abs(y - ref) / np.maximum(sc, 1e-300))))
+            checked["spmv"] += 1
+        elif r["kind"] == "cg" and checked["cg"] < 8:
+            bh = r["b"].cpu().numpy()
+            xh = r["x"].cpu().numpy()
+            cg_res = max(cg_res, float(np.linalg.norm(bh - oracle.csr_spmv(M["A"], xh)) / np.linalg.norm(bh)))
+            checked["cg"] += 1
     sat_base = serve_baseline(everything, [0.0] * len(everything))
-    # Poisson arrivals at fractions of the saturated request rate
     loads = []
-    half = everything[: max(1, len(everything) // 2)]
-    for frac in (0.25, 0.5, 0.75):
+    half = everything[: max(1, len(everything) * 2 // 3)]
+    for frac in fractions:
         rate = frac * sat["requests_per_s"]
         gaps = np.random.default_rng(int(frac * 100)).exponential(1.0 / rate, len(half))
         offsets = list(np.cumsum(gaps) - gaps[0])
@@ -1069,35 +1377,56 @@ def run_serving(args):
                       "argcsr_server": serve_ours(half, offsets),
                       "plain_csr_f64_fifo": serve_baseline(half, offsets)})
     total_nnz = int(sum(M["nnz"] for M in mats))
-    kinds = {}
-    for M in mats:
-        kinds.setdefault(M["kind"], [0, 0])
-        kinds[M["kind"]][0] += 1
-        kinds[M["kind"]][1] += M["nnz"]
-    out = {"metric": SERVE_METRIC, "unit": "solves/s", "higher_is_better": True, "n_gpus": 1,
-           "value": sat["cg_solves_per_s"], "dtype": "f32/bf16 storage, f32 inner CG, f64 refinement",
-           "data": "synthetic", "vs_baseline": None,
-           "config": {"workload": "64 matrices, n log-uniform in [1e4, 2e6] (Zipf members at most 5e4 "
-                                  "rows): 2D/3D Laplacians, symmetrised lognormal(1.8, 1.0) "
-                                  "diagonally dominant (SPD), Zipf(1.5) rows up to 50 000 entries "
-                                  "(SpMV only); FP32/BF16 alternating; requests 80% SpMV / 20% CG "
-                                  "(SPD members, tol 1e-8), x, b ~ U[-1,1]; HBM budget 150 GB",
-                      "requests": len(reqs), "streams": args.serve_streams,
-                      "pool_total_nnz": total_nnz,
-                      "pool_kinds": {k: {"matrices": v[0], "nnz": v[1]} for k, v in kinds.items()},
-                      "pool_generation_s": round(gen_s, 1)},
-           "saturation": {"argcsr_server": sat, "plain_csr_f64_fifo": sat_base},
-           "poisson": loads, "clocks": clock_info,
-           "gpu_launches": sat["gpu_launches"]}
-    print(json.dumps(out), flush=True)
     for M in mats:
         api.argcsr_destroy(M["h"], s)
         if M["hr"] is not None:
             api.argcsr_destroy(M["hr"], s)
     stream.synchronize()
+    p = loads[0] if loads else None
+    out = {"metric": SERVE_METRIC, "workload": SERVE_WORKLOAD, "requests": len(reqs), "streams": n_streams,
+           "pool_total_nnz": total_nnz,
+           "cg_solves_per_s": sat["cg_solves_per_s"],
+           "plain_csr_f64_cg_solves_per_s": sat_base["cg_solves_per_s"],
+           "p50_ms": p["argcsr_server"]["p50_ms"] if p else None,
+           "p99_ms": p["argcsr_server"]["p99_ms"] if p else None,
+           "plain_csr_f64_p50_ms": p["plain_csr_f64_fifo"]["p50_ms"] if p else None,
+           "plain_csr_f64_p99_ms": p["plain_csr_f64_fifo"]["p99_ms"] if p else None,
+           "latency_load": f"Poisson arrivals at {p['fraction_of_saturation']} of the saturated request rate"
+                           if p else None,
+           "err_vs_oracle": {"spmv_max": spmv_err, "spmv_results_checked": checked["spmv"],
+                             "spmv_measure": "max over 2048 sampled rows per result of |y - y_ref| / "
+                                             "sum|a x|, y_ref the oracle's FP64 product of the stored values",
+                             "cg_max_rel_residual_fp64": cg_res, "cg_results_checked": checked["cg"]},
+           "saturation": {"argcsr_server": sat, "plain_csr_f64_fifo": sat_base},
+           "poisson": loads, "clocks": clock_info, "gpu_launches": sat["gpu_launches"]}
+    if compact:
+        for side in out["saturation"].values():
+            for k in ("spmv_p50_ms", "spmv_p99_ms", "cg_p50_ms", "cg_p99_ms", "client_max_lag_ms"):
+                side.pop(k, None)
+    return out
 
 
-def run_ncu_case(which):
+def run_serving(args):
+    import torch
+    from paper_1203_5737_gb300 import argcsr as api
+    from paper_1203_5737_gb300 import build
+    build.build()
+    api.load_library()
+    t0 = time.time()
+    pool = synth.serving_pool(64, seed=0, workers=min(16, os.cpu_count() or 1))
+    gen_s = time.time() - t0
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    r = serving_measure(api, torch, dev, pool, args.requests, (0.25, 0.5, 0.75), args.serve_streams)
+    out = {"metric": SERVE_METRIC, "unit": "solves/s", "higher_is_better": True, "n_gpus": 1,
+           "value": r["cg_solves_per_s"], "dtype": "f32/bf16 storage, f32 inner CG, f64 refinement",
+           "data": "synthetic", "vs_baseline": None,
+           "config": {"workload": SERVE_WORKLOAD, "requests": args.requests, "streams": args.serve_streams,
+                      "pool_generation_s": round(gen_s, 1)}, **r}
+    print(json.dumps(out), flush=True)
+
+
+def run_ncu_case(which, ncu_d=None):
     """A short, untimed launch sequence for ncu captures: for each matrix, one
     conversion (k_tile_prepare, k_resolve, k_groups, k_tile_scan, k_fill) and
     two SpMVs.  'bench' uses the bench's two matrices; 'small' a 1,000,000-row
@@ -1151,7 +1480,11 @@ def run_ncu_case(which):
         print(f"ncu case {which}: ok")
         return
     if which == "bench":
-        mats = [(synth.workload(name)[0], D) for name, D in MATRICES]
+        Ds = dict(FALLBACK_D)
+        for item in filter(None, (ncu_d or "").split(",")):
+            k, v = item.split("=")
+            Ds[k] = int(v)
+        mats = [(synth.workload(name)[0], Ds[name]) for name in MATRICES]
     else:
         mats = [(synth.laplacian_3d(128), 8), (synth.lognormal_rows(1_000_000), 4)]
     for A, D in mats:
@@ -1178,7 +1511,7 @@ def main(argv=None):
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-sweep", action="store_true", help="skip the desiredChunkSize sweep")
-    p.add_argument("--cpu-seconds", type=float, default=10.0)
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--ncu-case", choices=("small", "bench", "cg", "batch"),
                    help="run a short untimed launch sequence for ncu, then exit")
     p.add_argument("--workload", choices=("uneven_fp64", "cg_poisson160", "batched4096", "serving"),
@@ -1187,12 +1520,20 @@ def main(argv=None):
                         "mixed-precision CG with FP64 refinement; batched4096: multi-RHS "
                         "products of 4096 matrices in one graph launch; serving: SpMV and "
                         "CG requests on a 64-matrix pool through the serving engine")
+    p.add_argument("--ncu-d", help="--ncu-case bench: desiredChunkSize per matrix, "
+                                   "e.g. lognormal_2m=8,laplace3d_128=16")
+    p.add_argument("--no-serving", action="store_true", help="leave the serving block out")
+    p.add_argument("--no-cg", action="store_true", help="leave the CG block out")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="take desiredChunkSize 8 for both matrices instead of the autotuner's choice")
+    p.add_argument("--requests-compact", type=int, default=300,
+                   help="requests of the default line's serving block")
     p.add_argument("--batch-count", type=int, default=4096)
     p.add_argument("--requests", type=int, default=600, help="serving: requests per saturation run")
     p.add_argument("--serve-streams", type=int, default=8, help="serving: stream slots")
     args = p.parse_args(argv)
     if args.ncu_case:
-        run_ncu_case(args.ncu_case)
+        run_ncu_case(args.ncu_case, args.ncu_d)
         return
     if args.workload == "cg_poisson160":
         run_cg(args)

@@ -171,6 +171,24 @@ ARGCSR_API argcsr_status argcsr_spmv_axpby(argcsr_t A, double alpha, const void 
                                            void *d_y, argcsr_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * argcsr_probe_gather -- a roofline probe for measurements; not an operation
+ * of the paper.  It makes the memory accesses of argcsr_spmv on A (Section 4:
+ * the group records, the padded column and value streams of Listing 1's
+ * layout, and one gather of x per stored column) without its arithmetic, so
+ * that its duration is the ceiling those accesses alone set.
+ *   mode & 3:        0 columns + x gathers; 1 columns + values + x gathers;
+ *                    2 columns only (no gathers)
+ *   (mode >> 2) & 3: the gather's load instruction: 0 read-only path,
+ *                    1 read-only without L1 allocation, 2 L2 only,
+ *                    3 default caching load
+ * Only G = 32, V = 1, ARGCSR_F64 handles (ARGCSR_ENOTSUP otherwise);
+ * other modes return ARGCSR_EINVAL.  d_x as in argcsr_spmv.  Writes no
+ * caller memory.  Asynchronous on `stream`; one kernel.
+ * ------------------------------------------------------------------------ */
+ARGCSR_API argcsr_status argcsr_probe_gather(argcsr_t A, const void *d_x, int32_t mode,
+                                             argcsr_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * argcsr_set_allocator -- device memory from the caller (for example a
  * framework's caching allocator) instead of the library's stream-ordered
  * pool, for every array the library allocates from then on: handles,

@@ -201,3 +201,45 @@ def argcsr_spmv(M: ArgCsr, x) -> np.ndarray:
                                           M.n_cols, M.G, M.V,
                                           _ptr(x), _ptr(y)), "argcsr_spmv")
     return y
+
+
+def argcsr_spmv_groups(M: ArgCsr, x, y, g0: int, g1: int) -> None:
+    """The Section 4 SpMV over groups [g0, g1) of M only, writing their rows
+    of ``y`` (float64[n_rows], caller-owned).  ``x`` must be contiguous
+    float64 and ``M.values`` float64.  Disjoint group ranges write disjoint
+    rows, so a caller may run several ranges at once on host threads (the
+    call releases the GIL); the arithmetic is that of argcsr_spmv."""
+    assert x.dtype == np.float64 and y.dtype == np.float64 and M.values.dtype == np.float64
+    assert 0 <= g0 <= g1 <= M.n_groups
+    if g1 == g0:
+        return
+    gi = M.groupInfo[g0:g1]
+    _check(_load().oracle_argcsr_spmv_f64(g1 - g0, _ptr(gi), _ptr(M.threadsMapping),
+                                          _ptr(M.columns), _ptr(M.values), M.n_slots,
+                                          M.n_cols, M.G, M.V, _ptr(x), _ptr(y)), "argcsr_spmv_groups")
+
+
+def round_to_bf16(v) -> np.ndarray:
+    """Round float64 values to bfloat16 (8 significant bits, FP32's exponent
+    range), nearest with ties to even, in ONE rounding from the given value;
+    returns the rounded values as float64.  This fixes the stored values of a
+    matrix kept in BF16 (the paper leaves the value type open, Sections 2-4;
+    the library stores narrower values rounded to nearest even).  Normal
+    values of binade [2^(e-1), 2^e) are quantised to multiples of 2^(e-8),
+    values below 2^-126 to multiples of 2^-133 (subnormals); results of
+    magnitude 2^128 or more overflow to infinity."""
+    v = np.asarray(v, dtype=np.float64)
+    out = v.copy()
+    fin = np.isfinite(v) & (v != 0)
+    _, e = np.frexp(v[fin])
+    q = np.maximum(e.astype(np.int64) - 8, -133)
+    r = np.ldexp(np.rint(np.ldexp(v[fin], -q)), q)
+    r[np.abs(r) >= 2.0 ** 128] = np.inf * np.sign(r[np.abs(r) >= 2.0 ** 128])
+    out[fin] = r
+    return out
+
+
+def bf16_bits(v) -> np.ndarray:
+    """The 16-bit patterns of bfloat16 values given exactly as float64."""
+    f = np.asarray(v, dtype=np.float64).astype(np.float32)
+    return (f.view(np.uint32) >> 16).astype(np.uint16)

@@ -90,6 +90,7 @@ _SIGNATURES = {
                                                  ctypes.POINTER(argcsr_params), _P, ctypes.POINTER(_P)]),
     "argcsr_spmv": (ctypes.c_int, [_P, _P, _P, _P]),
     "argcsr_spmv_axpby": (ctypes.c_int, [_P, ctypes.c_double, _P, ctypes.c_double, _P, _P]),
+    "argcsr_probe_gather": (ctypes.c_int, [_P, _P, _I32, _P]),
     "argcsr_set_allocator": (ctypes.c_int, [_P, _P, _P]),
     "argcsr_info": (ctypes.c_int, [_P, ctypes.POINTER(argcsr_info_t)]),
     "argcsr_export": (ctypes.c_int, [_P, _P, _P, _P, _P]),
@@ -328,6 +329,11 @@ def argcsr_convert_noalloc(n_rows, n_cols, nnz, d_rowPointers, d_columns, d_valu
         d_groupInfo, group_capacity, d_threadsMapping, d_out_columns, d_out_values, slot_capacity,
         ctypes.byref(ng), ctypes.byref(ns), stream)
     return st, ng.value, ns.value
+
+
+def argcsr_probe_gather(A, d_x, mode=0, stream=0) -> None:
+    """The SpMV's memory accesses without its arithmetic (a roofline probe)."""
+    _check(load_library().argcsr_probe_gather(A, d_x, mode, stream), "argcsr_probe_gather")
 
 
 def argcsr_spmm(A, k, d_X, ldx, d_Y, ldy, stream=0) -> None:

@@ -214,6 +214,18 @@ ARGCSR_API argcsr_status argcsr_spmv(argcsr_t A, const void *d_x, void *d_y, arg
     return launch_spmv(A, d_x, d_y, reinterpret_cast<cudaStream_t>(stream));
 }
 
+ARGCSR_API argcsr_status argcsr_probe_gather(argcsr_t A, const void *d_x, int32_t mode,
+                                             argcsr_stream_t stream) {
+    if (!A || mode < 0 || (mode & 3) == 3 || mode > 15) return ARGCSR_EINVAL;
+    if (A->G != 32 || A->V != 1 || A->dtype != ARGCSR_F64) {
+        set_error_message("argcsr_probe_gather: only G = 32, V = 1, f64 handles");
+        return ARGCSR_ENOTSUP;
+    }
+    if (A->n_rows == 0) return ARGCSR_OK;
+    if (!d_x && A->n_cols > 0 && (mode & 3) != 2) return ARGCSR_EINVAL;
+    return launch_probe_gather(A, d_x, mode, reinterpret_cast<cudaStream_t>(stream));
+}
+
 ARGCSR_API argcsr_status argcsr_set_allocator(argcsr_alloc_fn alloc, argcsr_free_fn free_fn, void *ctx) {
     if (!alloc != !free_fn) return ARGCSR_EINVAL;
     std::lock_guard<std::mutex> lock(g_alloc_mutex);

@@ -471,6 +471,21 @@ k_tile_scan(int numTiles, const long long *__restrict__ tileSlots, long long *__
 // 6. Group records and the chunk-wise copy (one warp per group).
 // ---------------------------------------------------------------------------
 
+// FP64 -> BF16 with one rounding to nearest even.  Going through FP32 with
+// two nearest roundings can land on a BF16 tie the FP64 value was not on
+// (then the tie goes to even, possibly the wrong way).  Rounding to FP32
+// towards zero and setting the last bit when that was inexact ("round to
+// odd", Boldo and Melquiond 2008) keeps the information a second rounding
+// needs: with 24 bits against BF16's 8, the RNE of the result to BF16 equals
+// the RNE of the FP64 value.  Out of FP32 range the truncation saturates at
+// the largest finite FP32 value, which rounds to infinity in BF16, as the
+// FP64 value does.
+__device__ __forceinline__ uint16_t bf16_from_double(double v) {
+    float f = __double2float_rz(v);
+    if ((double)f != v && v == v) f = __uint_as_float(__float_as_uint(f) | 1u);
+    return __bfloat16_as_ushort(__float2bfloat16_rn(f));
+}
+
 // A value of the input type in the storage type: a bit copy when the two
 // are the same; otherwise rounded to nearest even (BF16 is kept as its raw
 // 16 bits).
@@ -480,7 +495,7 @@ __device__ __forceinline__ VO to_storage(VI v) {
     else if constexpr (std::is_same<VO, float>::value && std::is_same<VI, double>::value)
         return __double2float_rn(v);
     else if constexpr (std::is_same<VO, uint16_t>::value && std::is_same<VI, double>::value)
-        return __bfloat16_as_ushort(__double2bfloat16(v));
+        return bf16_from_double(v);
     else {
         static_assert(std::is_same<VO, uint16_t>::value && std::is_same<VI, float>::value,
                       "unsupported value conversion");

@@ -39,6 +39,32 @@ __device__ __forceinline__ void ld_stream(const T *p, T (&out)[V]) {
     }
 }
 
+// Gather of one x element.  OP selects the load instruction: 0 the
+// read-only path (ld.global.nc), 1 the read-only path without allocating in
+// L1 (x lines are rarely reused there: a warp's 32 gathers hit 32 random
+// lines), 2 L2 only (ld.global.cg), 3 the default caching load.
+#ifndef ARGCSR_GATHER_OP
+#define ARGCSR_GATHER_OP 0
+#endif
+template <int OP = ARGCSR_GATHER_OP>
+__device__ __forceinline__ double ldx(const double *p) {
+    if constexpr (OP == 0) return __ldg(p);
+    double v;
+    if constexpr (OP == 1) asm("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    else if constexpr (OP == 2) asm("ld.global.cg.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    else asm("ld.global.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+template <int OP = ARGCSR_GATHER_OP>
+__device__ __forceinline__ float ldx(const float *p) {
+    if constexpr (OP == 0) return __ldg(p);
+    float v;
+    if constexpr (OP == 1) asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    else if constexpr (OP == 2) asm("ld.global.cg.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    else asm("ld.global.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
 // sum += v on lanes where `on` holds.  Written as a predicated PTX add so
 // that lanes without work issue no FP64 operation (a plain conditional add
 // may be turned into an add on every lane followed by a select).

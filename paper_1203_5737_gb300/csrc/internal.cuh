@@ -87,6 +87,7 @@ inline size_t vec_size(argcsr_dtype t) {  // element size of x and y
 }
 
 // Defined in spmv.cu: launch the ARG-CSR SpMV kernel for a handle.
+argcsr_status launch_probe_gather(const argcsr_matrix *A, const void *x, int mode, cudaStream_t s);
 argcsr_status launch_spmv(const argcsr_matrix *A, const void *x, void *y, cudaStream_t s);
 // One matrix of a batch (spmm.cu builds the array on the device).
 struct BatchDesc {

@@ -75,7 +75,7 @@ __device__ __forceinline__ void consume(const Batch<VT, V, U> &B, const AT *__re
     for (int u = 0; u < U; ++u)
 #pragma unroll
         for (int e = 0; e < V; ++e)
-            if (B.c[u][e] >= 0) sum = fma((AT)widen(B.v[u][e]), __ldg(x + B.c[u][e]), sum);
+            if (B.c[u][e] >= 0) sum = fma((AT)widen(B.v[u][e]), ldx(x + B.c[u][e]), sum);
 }
 
 // Sum of one chunk: C/V blocks of V elements; block b of chunk c starts at
@@ -181,7 +181,7 @@ __device__ __forceinline__ void group_fixed(const int4 info, const int *__restri
     const RowEnds m(tm, info.x, info.y, lane);
     AT xv[CC];
 #pragma unroll
-    for (int j = 0; j < CC; ++j) xv[j] = (m.owns && c[j] >= 0) ? __ldg(x + c[j]) : AT(0);
+    for (int j = 0; j < CC; ++j) xv[j] = (m.owns && c[j] >= 0) ? ldx(x + c[j]) : AT(0);
     AT sum = 0;
 #pragma unroll
     for (int j = 0; j < CC; ++j)
@@ -423,7 +423,78 @@ k_batch_spmv_g32(const BatchDesc *__restrict__ desc, const long long *__restrict
     reduce_store<0, AT>(sum, rm, info.x, lane, ep, y);
 }
 
+// Roofline probe: the memory accesses of k_spmv_g32 (G = 32, V = 1) without
+// its arithmetic.  Per group one record load, then for every slot row the
+// column stream (MODE 0 and 2), the value stream as well (MODE 1), and for
+// every column >= 0 one gather of x with load instruction OP (MODE 0 and 1;
+// MODE 2 reads the columns only).  The loaded bits are XOR-folded per lane
+// in integer registers and stored only if they equal a constant that no
+// input produces by chance: in practice nothing is written, and no load can
+// be dropped.  No FP64 instruction is issued.
+__device__ unsigned long long g_probe_sink;
+
+template <int MODE, int OP>
+__global__ void __launch_bounds__(256, 8)
+k_probe_g32(long long nGroups, const int4 *__restrict__ gi, const int *__restrict__ cols,
+            const double *__restrict__ vals, const double *__restrict__ x) {
+    constexpr int U = ARGCSR_SPMV_ELEMS;
+    const int lane = threadIdx.x & 31;
+    const long long g = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (g >= nGroups) return;   // warp-uniform
+    const int4 info = __ldg(gi + g);
+    const long long base = (long long)info.z + lane;
+    unsigned long long acc = 0;
+    for (int j = 0; j < info.w; j += U) {
+        int c[U];
+        double v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            c[u] = -1;
+            v[u] = 0.0;
+            if (j + u < info.w) {
+                c[u] = __ldcs(cols + base + 32LL * (j + u));
+                if constexpr (MODE == 1) v[u] = __ldcs(vals + base + 32LL * (j + u));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if constexpr (MODE == 2) {
+                acc ^= (unsigned)c[u];
+            } else if (c[u] >= 0) {
+                acc ^= (unsigned long long)__double_as_longlong(ldx<OP>(x + c[u]));
+                if constexpr (MODE == 1) acc ^= (unsigned long long)__double_as_longlong(v[u]);
+            }
+        }
+    }
+    if (acc == 0x5a5a5a5a5a5a5a5aULL) g_probe_sink = acc;
+}
+
+template <int MODE>
+void launch_probe_mode(unsigned blocks, const argcsr_matrix *A, const double *x, int op, cudaStream_t s) {
+    const auto *v = static_cast<const double *>(A->d_values);
+    switch (op) {
+        case 0: k_probe_g32<MODE, 0><<<blocks, 256, 0, s>>>(A->n_groups, A->d_groupInfo, A->d_columns, v, x); break;
+        case 1: k_probe_g32<MODE, 1><<<blocks, 256, 0, s>>>(A->n_groups, A->d_groupInfo, A->d_columns, v, x); break;
+        case 2: k_probe_g32<MODE, 2><<<blocks, 256, 0, s>>>(A->n_groups, A->d_groupInfo, A->d_columns, v, x); break;
+        default: k_probe_g32<MODE, 3><<<blocks, 256, 0, s>>>(A->n_groups, A->d_groupInfo, A->d_columns, v, x); break;
+    }
+}
+
 }  // namespace
+
+argcsr_status launch_probe_gather(const argcsr_matrix *A, const void *x, int mode, cudaStream_t s) {
+    if (A->n_groups == 0) return ARGCSR_OK;
+    const unsigned blocks = (unsigned)((A->n_groups + 7) / 8);
+    const int what = mode & 3, op = (mode >> 2) & 3;
+    const double *xx = static_cast<const double *>(x);
+    TraceScope t("k_probe_g32", s);
+    if (what == 0) launch_probe_mode<0>(blocks, A, xx, op, s);
+    else if (what == 1) launch_probe_mode<1>(blocks, A, xx, op, s);
+    else launch_probe_mode<2>(blocks, A, xx, op, s);
+    count_launches(1);
+    ARGCSR_CHECK_LAUNCH("k_probe_g32");
+    return ARGCSR_OK;
+}
 
 argcsr_status launch_batch_spmv(const BatchDesc *desc, const long long *groupPrefix, int nMat,
                                 long long totalGroups, argcsr_dtype dtype, const void *X, void *Y,

@@ -90,21 +90,44 @@ def test_single_rank_is_identity():
     assert bench.reduce_sum(7, 1) == 7.0
 
 
-def test_reference_step_on_a_small_sample():
+def test_oracle_work_split_over_threads_matches_one_call():
+    """The host baseline splits the oracle's product over threads by group
+    (ARG-CSR) and row (CSR) ranges; the result must be the one-call result
+    bit for bit, and the byte counts those of the bench's model."""
     oracle.build()
-    A = synth.lognormal_rows(5000, seed_structure=3)
+    A = synth.lognormal_rows(20000, seed_structure=3)
     x = synth.uniform_vector(A.n_cols, 1)
-    nbytes = bench.oracle_step([(A, x, 4)])
+    w = bench.OracleWork([("small", A, x, 4)], threads=3)
+    it = w.items[0]
     M = oracle.convert(A, 32, 4)
-    assert nbytes == (bench.conversion_bytes(A.n_rows, A.nnz, M.n_groups, M.n_slots)
-                      + bench.spmv_bytes(A.n_rows, A.n_cols, A.nnz, M.n_groups))
+    assert len(it["g_cuts"]) == 4 and it["g_cuts"][0] == 0 and it["g_cuts"][-1] == M.n_groups
+    assert sum(sl.n_rows for sl in it["csr_slices"]) == A.n_rows
+    nbytes = w.argcsr_step(3)
+    assert nbytes == bench.spmv_bytes(A.n_rows, A.n_cols, A.nnz, M.n_groups)
+    assert np.array_equal(it["y"], oracle.argcsr_spmv(M, x))
+    it["y"][:] = 0
+    w.argcsr_step(1)
+    assert np.array_equal(it["y"], oracle.argcsr_spmv(M, x))
+    assert w.csr_step(3) == bench.csr_spmv_bytes(A.n_rows, A.n_cols, A.nnz)
+    ys = np.concatenate([oracle.csr_spmv(sl, x) for sl in it["csr_slices"]])
+    assert np.array_equal(ys, oracle.csr_spmv(A, x))
 
 
-def test_row_prefix_sample():
-    A = synth.random_csr(100, 50, 2)
-    B = bench._row_prefix(A, 10)
-    assert B.n_rows == 10 and B.nnz == A.rowPointers[10]
-    assert np.array_equal(B.columns, A.columns[:B.nnz])
+def test_row_subset_sample():
+    A = synth.random_csr(100, 50, 2, p_empty=0.2)
+    rows = np.array([0, 3, 4, 50, 99])
+    B = bench._row_subset(A, rows)
+    assert B.n_rows == 5 and B.n_cols == A.n_cols
+    for i, r in enumerate(rows):
+        a, b = A.rowPointers[r], A.rowPointers[r + 1]
+        c, d = B.rowPointers[i], B.rowPointers[i + 1]
+        assert np.array_equal(B.columns[c:d], A.columns[a:b])
+        assert np.array_equal(B.values[c:d], A.values[a:b])
+
+
+def test_host_description():
+    h = bench.host_description()
+    assert h["nproc"] >= 1 and isinstance(h["cpu_model"], str) and h["cpu_model"]
 
 
 def test_reference_arm_other_ranks_do_no_work(monkeypatch, capsys):
@@ -121,11 +144,12 @@ def test_profile_figures_follow_the_kernel_sources(tmp_path, monkeypatch):
     (tmp_path / "profiles").mkdir()
     (tmp_path / "profiles" / "traffic.txt").write_text(
         "# comment\n"
-        f"k_spmv_g32 bench 123456 {digest}\n"
+        f"k_spmv_g32 bench_spmv 123456 {digest}\n"
         "k_fill bench 999 0000000000000000\n")
     (tmp_path / "profiles" / "limits.txt").write_text(
-        f"k_spmv_g32 l1tex_throughput_pct 31.5 80.5 {digest}\n"
-        "k_spmv_g32 fp64_pipe_active_pct 1.0 2.0 0000000000000000\n")
+        f"k_spmv_g32 l1tex_throughput_pct laplacian 31.5 {digest}\n"
+        f"k_spmv_g32 l1tex_throughput_pct lognormal 80.5 {digest}\n"
+        "k_spmv_g32 fp64_pipe_active_pct lognormal 2.0 0000000000000000\n")
     csrc = os.path.join(bench.ROOT, "paper_1203_5737_gb300", "csrc")
     real_root = bench.ROOT
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
@@ -133,8 +157,16 @@ def test_profile_figures_follow_the_kernel_sources(tmp_path, monkeypatch):
     (tmp_path / "paper_1203_5737_gb300").mkdir()
     os.symlink(csrc, tmp_path / "paper_1203_5737_gb300" / "csrc")
     assert bench.kernel_source_digest("k_spmv_g32") == digest
-    assert bench.ncu_traffic("k_spmv_g32") == 123456
-    assert bench.ncu_traffic("k_fill") is None
+    assert bench.ncu_traffic("k_spmv_g32", "bench_spmv") == 123456
+    assert bench.ncu_traffic("k_spmv_g32", "bench") is None
+    assert bench.ncu_traffic("k_fill", "bench") is None
     assert bench.ncu_limits("k_spmv_g32") == {"l1tex_throughput_pct": {"laplacian": 31.5, "lognormal": 80.5}}
-    assert bench.ncu_traffic("k_unknown") is None
+    assert bench.ncu_traffic("k_unknown", "bench") is None
     monkeypatch.setattr(bench, "ROOT", real_root)
+
+
+def test_digest_ignores_comments():
+    code = "int f(int a) { return a + 1; }  // add one\n"
+    assert bench.strip_comments(code) == bench.strip_comments(
+        "/* a block\n comment */\n" + code.replace("// add one", "// another note") + "\n\n")
+    assert bench.strip_comments(code) != bench.strip_comments(code.replace("+ 1", "+ 2"))

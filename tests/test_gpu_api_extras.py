@@ -37,7 +37,11 @@ def test_storage_conversion_is_round_to_nearest(src, dst, G, V):
     tdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}
     A = synth.random_csr(2500, 1800, G + V, mean_len=9, n_huge=2, huge_len=900)
     vin = torch.from_numpy(A.values).to(tdt[src])
-    vstored = vin.to(tdt[dst])                       # torch's round-to-nearest-even on the CPU
+    if (src, dst) == ("f64", "bf16"):
+        # one rounding from FP64 (torch's CPU conversion rounds through FP32)
+        vstored = torch.from_numpy(oracle.round_to_bf16(vin.numpy())).to(torch.bfloat16)
+    else:
+        vstored = vin.to(tdt[dst])                   # torch's round-to-nearest-even on the CPU
     rp = torch.from_numpy(A.rowPointers).to(DEV)
     cols = torch.from_numpy(A.columns).to(DEV)
     with ArgCsrMatrix.from_csr(rp, cols, vin.to(DEV), A.n_cols, group_size=G, desired_chunk_size=4,
@@ -50,6 +54,26 @@ def test_storage_conversion_is_round_to_nearest(src, dst, G, V):
         assert np.array_equal(got["columns"], ref.columns)
         assert np.array_equal(got["threadsMapping"], ref.threadsMapping)
         assert np.array_equal(got["values"].view(np.uint8), ref.values.view(np.uint8))
+
+
+def test_fp64_to_bf16_is_one_rounding():
+    """Values just off a BF16 tie, where rounding through FP32 first would land
+    on the tie: the stored BF16 must be the nearest one to the FP64 value."""
+    rng = np.random.default_rng(9)
+    n = 40000
+    base = np.ldexp(1.0 + (rng.integers(0, 128, n) + 0.5) / 128.0, rng.integers(-60, 60, n))
+    off = np.ldexp(rng.choice([-1.0, 1.0], n), rng.integers(-40, -25, n)) * base
+    vals = np.concatenate([base + off, base, rng.standard_normal(n)]) * rng.choice([-1.0, 1.0], 3 * n)
+    m = vals.size
+    A = synth.Csr(m, 1, np.arange(m + 1, dtype=np.int32), np.zeros(m, dtype=np.int32), vals)
+    rp = torch.from_numpy(A.rowPointers).to(DEV)
+    cols = torch.from_numpy(A.columns).to(DEV)
+    with ArgCsrMatrix.from_csr(rp, cols, torch.from_numpy(vals).to(DEV), 1, group_size=32,
+                               desired_chunk_size=1, storage_dtype=torch.bfloat16) as M:
+        got = M.export()
+    ref = oracle.convert(synth.Csr(m, 1, A.rowPointers, A.columns,
+                                   oracle.bf16_bits(oracle.round_to_bf16(vals))), 32, 1)
+    assert np.array_equal(got["values"].view(np.uint16), ref.values.view(np.uint16))
 
 
 def test_unsupported_widening_is_refused():

@@ -486,3 +486,39 @@ def test_empty_matrix():
     assert M.n_groups == 2 and M.n_slots == 0
     assert np.array_equal(M.groupInfo[:, 3], [0, 0])
     assert np.array_equal(oracle.argcsr_spmv(M, np.ones(40)), np.zeros(40))
+
+
+def test_bf16_rounding_single_and_to_even():
+    """oracle.round_to_bf16 against values fixed by the definition: exact
+    values stay, ties go to the even neighbour, and a value just off a tie
+    goes to the nearer neighbour even when rounding to FP32 first would put
+    it on the tie (the double-rounding case)."""
+    u = 2.0 ** -7                      # BF16 spacing in [1, 2)
+    cases = {1.0: 1.0, 1.0 + u: 1.0 + u, -3.0: -3.0, 0.0: 0.0,
+             1.0 + u / 2: 1.0,                       # tie -> even (1.0)
+             1.0 + 3 * u / 2: 1.0 + 2 * u,           # tie -> even (1 + 2u)
+             1.0 + u / 2 + 2.0 ** -30: 1.0 + u,      # just above the tie
+             1.0 + u / 2 - 2.0 ** -30: 1.0,          # just below the tie
+             -(1.0 + u / 2 + 2.0 ** -30): -(1.0 + u),
+             2.0 ** 127 * (2 - u / 2): np.inf,       # halfway to 2^128: overflows
+             2.0 ** 127 * (2 - u): 2.0 ** 127 * (2 - u),   # largest finite
+             2.0 ** -133: 2.0 ** -133,               # smallest subnormal
+             2.0 ** -134: 0.0,                       # tie with 0 -> even (0)
+             3 * 2.0 ** -134: 2.0 ** -132}           # tie -> even (2 * 2^-133)
+    got = oracle.round_to_bf16(np.array(list(cases)))
+    assert np.array_equal(got, np.array(list(cases.values())))
+    assert np.isnan(oracle.round_to_bf16(np.array([np.nan]))[0])
+
+
+def test_bf16_rounding_of_fp32_values_matches_torch():
+    """From FP32 a single rounding is all there is, so torch's FP32 -> BF16
+    conversion is an independent reference there."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(4)
+    v32 = np.concatenate([rng.standard_normal(200000), rng.standard_normal(20000) * 1e30,
+                          rng.standard_normal(20000) * 1e-38]).astype(np.float32)
+    ref = torch.from_numpy(v32).to(torch.bfloat16).to(torch.float64).numpy()
+    got = oracle.round_to_bf16(v32.astype(np.float64))
+    assert np.array_equal(got, ref)
+    assert np.array_equal(oracle.bf16_bits(got),
+                          torch.from_numpy(v32).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16))

@@ -238,23 +238,13 @@ __device__ __forceinline__ void long_group_block(const int4 info, const int *__r
 // matrices).  The loop for chunks above 8 spills too much at 32, so
 // matrices whose mean chunk size is above 8 get 40 (WIDE true), as do FP64
 // V = 2; V = 4, whose wider loads need more, gets 51.
-template <typename VT, typename AT, int V, int MODE, bool WIDE>
-__global__ void __launch_bounds__(256, sizeof(AT) == 4 ? 8 : (V == 1 && !WIDE ? 8 : V == 4 ? 5 : 6))
-k_spmv_g32(long long nGroups, const int4 *__restrict__ gi, const int *__restrict__ tm,
-           const int *__restrict__ cols, const VT *__restrict__ vals, const AT *__restrict__ x,
-           const Epi<AT> ep, AT *__restrict__ y, const int *__restrict__ longList, int nLong) {
-    using Acc = AT;
+// One G = 32 group on one warp (info = its record).
+template <typename VT, typename AT, int V, int MODE>
+__device__ __forceinline__ void group_g32(const int4 info, const int *__restrict__ tm,
+                                          const int *__restrict__ cols, const VT *__restrict__ vals,
+                                          const AT *__restrict__ x, const Epi<AT> &ep, AT *__restrict__ y,
+                                          int nLong, int lane) {
     constexpr int U = (ARGCSR_SPMV_ELEMS + V - 1) / V;
-    const int lane = threadIdx.x & 31;
-    if constexpr (V == 1) {
-        if ((int)blockIdx.x < nLong) {   // block-uniform: the long groups first
-            long_group_block<VT, AT, MODE>(__ldg(gi + __ldg(longList + blockIdx.x)), tm, cols, vals, x, ep, y);
-            return;
-        }
-    }
-    const long long g = (long long)(blockIdx.x - nLong) * 8 + (threadIdx.x >> 5);
-    if (g >= nGroups) return;  // warp-uniform
-    const int4 info = __ldg(gi + g);  // firstRow, size, offset, chunkSize
     const int first = info.x, size = info.y, C = info.w;
 #if ARGCSR_SPMV_FIXED
     if constexpr (V == 1) {
@@ -277,8 +267,34 @@ k_spmv_g32(long long nGroups, const int4 *__restrict__ gi, const int *__restrict
     Batch<VT, V, U> B;
     load_batch<VT, V, U>(B, cols + base, vals + base, 32LL * V, 0, C / V, true);
     const RowEnds m(tm, first, size, lane);
-    Acc sum = chunk_sum<32, VT, AT, V>(cols, vals, x, base, C, m.owns, B);
+    AT sum = chunk_sum<32, VT, AT, V>(cols, vals, x, base, C, m.owns, B);
     reduce_store<MODE, AT>(sum, m, first, lane, ep, y);
+}
+
+// G = 32: one warp per group.
+// y = A x, or y = b - A x when b is given (the residual of a solver).
+// Register budgets: 32, so that 64 warps fit on an SM (the gathers need
+// every warp in flight), with FP32 accumulation, and with FP64 for V = 1
+// when most groups take the unrolled path (WIDE false; a few registers
+// spill to L1, and 40 registers with 48 warps were 5 % slower on both bench
+// matrices).  The loop for chunks above 8 spills too much at 32, so
+// matrices whose mean chunk size is above 8 get 40 (WIDE true), as do FP64
+// V = 2; V = 4, whose wider loads need more, gets 51.
+template <typename VT, typename AT, int V, int MODE, bool WIDE>
+__global__ void __launch_bounds__(256, sizeof(AT) == 4 ? 8 : (V == 1 && !WIDE ? 8 : V == 4 ? 5 : 6))
+k_spmv_g32(long long nGroups, const int4 *__restrict__ gi, const int *__restrict__ tm,
+           const int *__restrict__ cols, const VT *__restrict__ vals, const AT *__restrict__ x,
+           const Epi<AT> ep, AT *__restrict__ y, const int *__restrict__ longList, int nLong) {
+    const int lane = threadIdx.x & 31;
+    if constexpr (V == 1) {
+        if ((int)blockIdx.x < nLong) {   // block-uniform: the long groups first
+            long_group_block<VT, AT, MODE>(__ldg(gi + __ldg(longList + blockIdx.x)), tm, cols, vals, x, ep, y);
+            return;
+        }
+    }
+    const long long g = (long long)(blockIdx.x - nLong) * 8 + (threadIdx.x >> 5);
+    if (g >= nGroups) return;  // warp-uniform
+    group_g32<VT, AT, V, MODE>(__ldg(gi + g), tm, cols, vals, x, ep, y, nLong, lane);
 }
 
 // G = 64 or 128: one group per G threads, 256 / G groups per block.
@@ -319,6 +335,13 @@ k_spmv_block(long long nGroups, const int4 *__restrict__ gi, const int *__restri
     }
 }
 
+template <typename VT, typename AT, int V, int MODE, bool WIDE>
+void launch_g32(long long ng, const int4 *gi, const int *tm, const int *cols, const VT *vals, const AT *x,
+                const Epi<AT> &ep, AT *y, const int *longList, int nLong, cudaStream_t s) {
+    k_spmv_g32<VT, AT, V, MODE, WIDE><<<(unsigned)((ng + 7) / 8 + nLong), 256, 0, s>>>(
+        ng, gi, tm, cols, vals, x, ep, y, longList, nLong);
+}
+
 template <typename VT, typename AT, int V, int MODE>
 argcsr_status launch_typed(const argcsr_matrix *A, const void *x, const Epi<AT> &ep, void *y,
                            cudaStream_t s) {
@@ -335,19 +358,17 @@ argcsr_status launch_typed(const argcsr_matrix *A, const void *x, const Epi<AT> 
     const int nLong = V == 1 && A->G == 32 ? (int)A->n_long : 0;
     switch (A->G) {
         case 32: {
-            const unsigned blocks = (unsigned)((ng + 7) / 8 + nLong);
             bool wide = false;
             // FP64, V = 1, mean chunk size S / (32 groups) above 8: mostly the looped path
             if constexpr (sizeof(AT) == 8 && V == 1) wide = A->n_slots > 8LL * 32 * ng;
             if constexpr (sizeof(AT) == 8 && V == 1) {
                 if (wide) {
-                    k_spmv_g32<VT, AT, V, MODE, true><<<blocks, 256, 0, s>>>(ng, gi, tm, cols, vals, xx, ep,
-                                                                             yy, A->d_longGroups, nLong);
+                    launch_g32<VT, AT, V, MODE, true>(ng, gi, tm, cols, vals, xx, ep, yy, A->d_longGroups,
+                                                      nLong, s);
                     break;
                 }
             }
-            k_spmv_g32<VT, AT, V, MODE, false><<<blocks, 256, 0, s>>>(ng, gi, tm, cols, vals, xx, ep, yy,
-                                                                      A->d_longGroups, nLong);
+            launch_g32<VT, AT, V, MODE, false>(ng, gi, tm, cols, vals, xx, ep, yy, A->d_longGroups, nLong, s);
             break;
         }
         case 64: k_spmv_block<64, VT, AT, V, MODE><<<(unsigned)((ng + 3) / 4), 256, 0, s>>>(ng, gi, tm, cols, vals, xx, ep, yy); break;

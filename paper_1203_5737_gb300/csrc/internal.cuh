@@ -97,10 +97,14 @@ struct BatchDesc {
     const void *vals;
     long long rowBase;   // first row of this matrix in the packed Y
     long long colBase;   // first row of this matrix in the packed X
+    long long nGroups;   // groups of this matrix
+    int nCols;           // columns of this matrix
+    int reserved;
 };
-// y = A x for every matrix of a batch (k = 1, G = 32, V = 1), one warp per
-// group of the concatenated group list (spmv.cu).
-argcsr_status launch_batch_spmv(const BatchDesc *desc, const long long *groupPrefix, int nMat,
+// y = A x for every matrix of a batch (k = 1, G = 32, V = 1): one block per
+// matrix in `order`, x staged in shared memory when it fits (spmv.cu).
+argcsr_status prepare_batch_spmv();
+argcsr_status launch_batch_spmv(const BatchDesc *desc, const int *order, int count, int maxCols,
                                 long long totalGroups, argcsr_dtype dtype, const void *X, void *Y,
                                 cudaStream_t s);
 // y = alpha A x + beta y (y not read when beta is 0).

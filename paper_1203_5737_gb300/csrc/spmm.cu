@@ -16,6 +16,8 @@
 
 #include <vector>
 
+#include <algorithm>
+
 #include "device.cuh"
 #include "internal.cuh"
 
@@ -27,6 +29,8 @@ struct argcsr_batch {
     int64_t total_rows, total_cols, total_groups, total_nnz, total_slots;
     void *d_desc;                 // BatchDesc[count]
     long long *d_groupPrefix;     // count + 1
+    int *d_order;                 // members by stored slots, most first (count)
+    int maxCols;                  // largest member's column count
     std::vector<int64_t> rowOff, colOff;   // host prefix sums (count + 1)
 };
 
@@ -523,7 +527,7 @@ argcsr_status launch_spmm(const argcsr_matrix *A, int k, const void *X, long lon
 argcsr_status launch_batch(const argcsr_batch *B, int k, const void *X, void *Y, cudaStream_t s) {
     if (B->total_groups == 0) return ARGCSR_OK;
     if (k == 1 && B->V == 1)   // one warp per group, the single-matrix product's code
-        return launch_batch_spmv(static_cast<const BatchDesc *>(B->d_desc), B->d_groupPrefix, B->count,
+        return launch_batch_spmv(static_cast<const BatchDesc *>(B->d_desc), B->d_order, B->count, B->maxCols,
                                  B->total_groups, B->dtype, X, Y, s);
     TraceScope t("k_batch_spmm_g32", s);
     argcsr_status st;
@@ -585,7 +589,8 @@ ARGCSR_API argcsr_status argcsr_batch_create(int32_t count, const argcsr_t *mats
     for (int i = 0; i < count; ++i) {
         const argcsr_matrix *A = mats[i];
         desc[i] = BatchDesc{A->d_groupInfo, A->d_threadsMapping, A->d_columns, A->d_values,
-                            B->rowOff[i], B->colOff[i]};
+                            B->rowOff[i], B->colOff[i], A->n_groups, A->n_cols, 0};
+        B->maxCols = std::max(B->maxCols, (int)A->n_cols);
         prefix[i + 1] = prefix[i] + A->n_groups;
         B->rowOff[i + 1] = B->rowOff[i] + A->n_rows;
         B->colOff[i + 1] = B->colOff[i] + A->n_cols;
@@ -595,17 +600,28 @@ ARGCSR_API argcsr_status argcsr_batch_create(int32_t count, const argcsr_t *mats
     B->total_rows = B->rowOff[count];
     B->total_cols = B->colOff[count];
     B->total_groups = prefix[count];
-    argcsr_status st = pool_alloc(&B->d_desc, sizeof(BatchDesc) * count, s);
+    // the members with the most slots first: the k = 1 product gives each
+    // member a block, and the long ones should not start last
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return mats[a]->n_slots > mats[b]->n_slots; });
+    argcsr_status st = prepare_batch_spmv();
+    if (st == ARGCSR_OK) st = pool_alloc(&B->d_desc, sizeof(BatchDesc) * count, s);
     if (st == ARGCSR_OK) st = pool_alloc((void **)&B->d_groupPrefix, sizeof(long long) * (count + 1), s);
+    if (st == ARGCSR_OK) st = pool_alloc((void **)&B->d_order, sizeof(int) * count, s);
     cudaError_t e = cudaSuccess;
     if (st == ARGCSR_OK) e = cudaMemcpyAsync(B->d_desc, desc.data(), sizeof(BatchDesc) * count, cudaMemcpyHostToDevice, s);
     if (st == ARGCSR_OK && e == cudaSuccess)
         e = cudaMemcpyAsync(B->d_groupPrefix, prefix.data(), sizeof(long long) * (count + 1), cudaMemcpyHostToDevice, s);
+    if (st == ARGCSR_OK && e == cudaSuccess)
+        e = cudaMemcpyAsync(B->d_order, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s);
     if (st == ARGCSR_OK && e == cudaSuccess) e = cudaStreamSynchronize(s);  // host vectors go out of scope
     if (st == ARGCSR_OK && e != cudaSuccess) st = record_cuda(e, "argcsr_batch_create");
     if (st != ARGCSR_OK) {
         pool_free(B->d_desc, s);
         pool_free(B->d_groupPrefix, s);
+        pool_free(B->d_order, s);
         delete B;
         return st;
     }
@@ -696,6 +712,7 @@ ARGCSR_API argcsr_status argcsr_batch_destroy(argcsr_batch_t B, argcsr_stream_t 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     pool_free(B->d_desc, s);
     pool_free(B->d_groupPrefix, s);
+    pool_free(B->d_order, s);
     delete B;
     return ARGCSR_OK;
 }

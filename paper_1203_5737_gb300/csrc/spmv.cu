@@ -23,6 +23,8 @@
 //    (column -1) rather than by a whole-warp exit: with the minimal chunk
 //    size some chunk of every group is full, so a warp never runs out of
 //    work before the last element row.
+#include <algorithm>
+
 #include "device.cuh"
 #include "internal.cuh"
 
@@ -66,16 +68,35 @@ __device__ __forceinline__ void load_batch(Batch<VT, V, U> &B, const int *__rest
     }
 }
 
+// Where x is gathered from: global memory (ldx), or a copy in shared memory
+// at a 32-bit shared-window address (an explicit ld.shared).
+template <typename AT>
+struct XGlobal {
+    const AT *__restrict__ p;
+    __device__ __forceinline__ AT operator()(int c) const { return ldx(p + c); }
+};
+template <typename AT>
+struct XShared {
+    unsigned base;
+    __device__ __forceinline__ AT operator()(int c) const {
+        AT v;
+        if constexpr (sizeof(AT) == 8)
+            asm("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(base + 8u * (unsigned)c));
+        else
+            asm("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(base + 4u * (unsigned)c));
+        return v;
+    }
+};
+
 // sum += v * x[col] over a batch, in the accumulation type AT (values are
 // widened exactly: bf16 -> f32 -> AT, f32 -> AT).
-template <typename VT, typename AT, int V, int U>
-__device__ __forceinline__ void consume(const Batch<VT, V, U> &B, const AT *__restrict__ x,
-                                        AT &sum) {
+template <typename VT, typename AT, int V, int U, typename XG>
+__device__ __forceinline__ void consume(const Batch<VT, V, U> &B, const XG &xg, AT &sum) {
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
         for (int e = 0; e < V; ++e)
-            if (B.c[u][e] >= 0) sum = fma((AT)widen(B.v[u][e]), ldx(x + B.c[u][e]), sum);
+            if (B.c[u][e] >= 0) sum = fma((AT)widen(B.v[u][e]), xg(B.c[u][e]), sum);
 }
 
 // Sum of one chunk: C/V blocks of V elements; block b of chunk c starts at
@@ -83,9 +104,9 @@ __device__ __forceinline__ void consume(const Batch<VT, V, U> &B, const AT *__re
 // rest are loaded only by lanes that own a row.  A minimal chunk size leaves
 // at least one chunk of the group full, so the loop runs all C/V blocks (the
 // paper's whole-warp early exit at padding would never fire).
-template <int G, typename VT, typename AT, int V>
+template <int G, typename VT, typename AT, int V, typename XG>
 __device__ __forceinline__ AT
-chunk_sum(const int *__restrict__ cols, const VT *__restrict__ vals, const AT *__restrict__ x,
+chunk_sum(const int *__restrict__ cols, const VT *__restrict__ vals, const XG &x,
           long long base, int C, bool owns, Batch<VT, V, (ARGCSR_SPMV_ELEMS + V - 1) / V> &B) {
     constexpr int U = (ARGCSR_SPMV_ELEMS + V - 1) / V;
     AT sum = 0;
@@ -97,10 +118,10 @@ chunk_sum(const int *__restrict__ cols, const VT *__restrict__ vals, const AT *_
 #if ARGCSR_SPMV_PREFETCH
         Batch<VT, V, U> N;
         load_batch<VT, V, U>(N, cp, vp, stride, b + U, nb, owns);
-        consume<VT, AT, V, U>(B, x, sum);
+        consume<VT, AT, V, U, XG>(B, x, sum);
         B = N;
 #else
-        consume<VT, AT, V, U>(B, x, sum);
+        consume<VT, AT, V, U, XG>(B, x, sum);
         load_batch<VT, V, U>(B, cp, vp, stride, b + U, nb, owns);
 #endif
     }
@@ -161,10 +182,10 @@ __device__ __forceinline__ void reduce_store(AT sum, const RowEnds &m, int first
 // all its slot loads at once, before threadsMapping is known, then all its
 // x gathers, and spends no multiply-add on slot rows past the chunk.  The
 // multiply-adds run in slot order, as in the batched loop.
-template <int CC, int MODE, typename VT, typename AT>
+template <int CC, int MODE, typename VT, typename AT, typename XG>
 __device__ __forceinline__ void group_fixed(const int4 info, const int *__restrict__ tm,
                                             const int *__restrict__ cols, const VT *__restrict__ vals,
-                                            const AT *__restrict__ x, const Epi<AT> &ep,
+                                            const XG &x, const Epi<AT> &ep,
                                             AT *__restrict__ y, int lane) {
     const long long base = (long long)info.z + lane;
     int c[CC];
@@ -181,7 +202,7 @@ __device__ __forceinline__ void group_fixed(const int4 info, const int *__restri
     const RowEnds m(tm, info.x, info.y, lane);
     AT xv[CC];
 #pragma unroll
-    for (int j = 0; j < CC; ++j) xv[j] = (m.owns && c[j] >= 0) ? ldx(x + c[j]) : AT(0);
+    for (int j = 0; j < CC; ++j) xv[j] = (m.owns && c[j] >= 0) ? x(c[j]) : AT(0);
     AT sum = 0;
 #pragma unroll
     for (int j = 0; j < CC; ++j)
@@ -218,7 +239,7 @@ __device__ __forceinline__ void long_group_block(const int4 info, const int *__r
     for (int b = 0; b < nb; b += U) {
         Batch<VT, 1, U> N;
         load_batch<VT, 1, U>(N, cp, vp, 32LL, b + U, nb, true);
-        consume<VT, AT, 1, U>(B, x, sum);
+        consume<VT, AT, 1, U, XGlobal<AT>>(B, XGlobal<AT>{x}, sum);
         B = N;
     }
     partial[warp][lane] = sum;
@@ -246,17 +267,18 @@ __device__ __forceinline__ void group_g32(const int4 info, const int *__restrict
                                           int nLong, int lane) {
     constexpr int U = (ARGCSR_SPMV_ELEMS + V - 1) / V;
     const int first = info.x, size = info.y, C = info.w;
+    const XGlobal<AT> xg{x};
 #if ARGCSR_SPMV_FIXED
     if constexpr (V == 1) {
         switch (C) {   // warp-uniform
-            case 1: group_fixed<1, MODE>(info, tm, cols, vals, x, ep, y, lane); return;
-            case 2: group_fixed<2, MODE>(info, tm, cols, vals, x, ep, y, lane); return;
-            case 3: group_fixed<3, MODE>(info, tm, cols, vals, x, ep, y, lane); return;
-            case 4: group_fixed<4, MODE>(info, tm, cols, vals, x, ep, y, lane); return;
-            case 5: group_fixed<5, MODE>(info, tm, cols, vals, x, ep, y, lane); return;
-            case 6: group_fixed<6, MODE>(info, tm, cols, vals, x, ep, y, lane); return;
-            case 7: group_fixed<7, MODE>(info, tm, cols, vals, x, ep, y, lane); return;
-            case 8: group_fixed<8, MODE>(info, tm, cols, vals, x, ep, y, lane); return;
+            case 1: group_fixed<1, MODE>(info, tm, cols, vals, xg, ep, y, lane); return;
+            case 2: group_fixed<2, MODE>(info, tm, cols, vals, xg, ep, y, lane); return;
+            case 3: group_fixed<3, MODE>(info, tm, cols, vals, xg, ep, y, lane); return;
+            case 4: group_fixed<4, MODE>(info, tm, cols, vals, xg, ep, y, lane); return;
+            case 5: group_fixed<5, MODE>(info, tm, cols, vals, xg, ep, y, lane); return;
+            case 6: group_fixed<6, MODE>(info, tm, cols, vals, xg, ep, y, lane); return;
+            case 7: group_fixed<7, MODE>(info, tm, cols, vals, xg, ep, y, lane); return;
+            case 8: group_fixed<8, MODE>(info, tm, cols, vals, xg, ep, y, lane); return;
             default: break;
         }
     }
@@ -267,7 +289,7 @@ __device__ __forceinline__ void group_g32(const int4 info, const int *__restrict
     Batch<VT, V, U> B;
     load_batch<VT, V, U>(B, cols + base, vals + base, 32LL * V, 0, C / V, true);
     const RowEnds m(tm, first, size, lane);
-    AT sum = chunk_sum<32, VT, AT, V>(cols, vals, x, base, C, m.owns, B);
+    AT sum = chunk_sum<32, VT, AT, V>(cols, vals, xg, base, C, m.owns, B);
     reduce_store<MODE, AT>(sum, m, first, lane, ep, y);
 }
 
@@ -326,7 +348,7 @@ k_spmv_block(long long nGroups, const int4 *__restrict__ gi, const int *__restri
     const long long base = (long long)info.z + c * V;
     Batch<VT, V, U> B;
     load_batch<VT, V, U>(B, cols + base, vals + base, (long long)G * V, 0, C / V, owns);
-    partial[threadIdx.x] = chunk_sum<G, VT, AT, V>(cols, vals, x, base, C, owns, B);
+    partial[threadIdx.x] = chunk_sum<G, VT, AT, V>(cols, vals, XGlobal<AT>{x}, base, C, owns, B);
     __syncthreads();
     if (c < size) {
         Acc s = partial[sub * G + begin];
@@ -393,46 +415,22 @@ Epi<AT> epi(const void *b = nullptr, double alpha = 1.0, double beta = 0.0) {
     return Epi<AT>{static_cast<const AT *>(b), (AT)alpha, (AT)beta};
 }
 
-// Every group of a batch of matrices, one warp per group as in k_spmv_g32
-// (k = 1, V = 1).  A block's 8 groups are consecutive in the concatenated
-// list, so one binary search over the matrices' group prefix per block
-// finds the first one's matrix; a warp walks forward from there.
-template <typename VT, typename AT>
-__global__ void __launch_bounds__(256, sizeof(AT) == 4 ? 8 : 6)
-k_batch_spmv_g32(const BatchDesc *__restrict__ desc, const long long *__restrict__ groupPrefix,
-                 int nMat, long long totalGroups, const AT *__restrict__ X, AT *__restrict__ Y) {
-    __shared__ int s_m;
-    const long long g0 = (long long)blockIdx.x * 8;
-    if (threadIdx.x == 0) {
-        int lo = 0, hi = nMat - 1;   // last m with groupPrefix[m] <= g0
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(groupPrefix + mid) <= g0) lo = mid; else hi = mid - 1;
-        }
-        s_m = lo;
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const long long g = g0 + (threadIdx.x >> 5);
-    if (g >= totalGroups) return;   // warp-uniform
-    int m = s_m;
-    while (g >= __ldg(groupPrefix + m + 1)) ++m;
-    const BatchDesc d = desc[m];
-    const int4 info = __ldg(d.gi + (g - __ldg(groupPrefix + m)));
-    const int *tm = d.tm, *cols = d.cols;
-    const VT *vals = static_cast<const VT *>(d.vals);
-    const AT *x = X + d.colBase;
-    AT *y = Y + d.rowBase;
+// One G = 32 group of a batch member on one warp (k = 1, V = 1), gathering x
+// through xg: the single-matrix product's code, a long group included.
+template <typename VT, typename AT, typename XG>
+__device__ __forceinline__ void batch_group(const int4 info, const int *__restrict__ tm,
+                                            const int *__restrict__ cols, const VT *__restrict__ vals,
+                                            const XG &xg, AT *__restrict__ y, int lane) {
     const Epi<AT> ep{nullptr, AT(1), AT(0)};
     switch (info.w) {   // warp-uniform
-        case 1: group_fixed<1, 0>(info, tm, cols, vals, x, ep, y, lane); return;
-        case 2: group_fixed<2, 0>(info, tm, cols, vals, x, ep, y, lane); return;
-        case 3: group_fixed<3, 0>(info, tm, cols, vals, x, ep, y, lane); return;
-        case 4: group_fixed<4, 0>(info, tm, cols, vals, x, ep, y, lane); return;
-        case 5: group_fixed<5, 0>(info, tm, cols, vals, x, ep, y, lane); return;
-        case 6: group_fixed<6, 0>(info, tm, cols, vals, x, ep, y, lane); return;
-        case 7: group_fixed<7, 0>(info, tm, cols, vals, x, ep, y, lane); return;
-        case 8: group_fixed<8, 0>(info, tm, cols, vals, x, ep, y, lane); return;
+        case 1: group_fixed<1, 0>(info, tm, cols, vals, xg, ep, y, lane); return;
+        case 2: group_fixed<2, 0>(info, tm, cols, vals, xg, ep, y, lane); return;
+        case 3: group_fixed<3, 0>(info, tm, cols, vals, xg, ep, y, lane); return;
+        case 4: group_fixed<4, 0>(info, tm, cols, vals, xg, ep, y, lane); return;
+        case 5: group_fixed<5, 0>(info, tm, cols, vals, xg, ep, y, lane); return;
+        case 6: group_fixed<6, 0>(info, tm, cols, vals, xg, ep, y, lane); return;
+        case 7: group_fixed<7, 0>(info, tm, cols, vals, xg, ep, y, lane); return;
+        case 8: group_fixed<8, 0>(info, tm, cols, vals, xg, ep, y, lane); return;
         default: break;
     }
     constexpr int U = ARGCSR_SPMV_ELEMS;
@@ -440,8 +438,41 @@ k_batch_spmv_g32(const BatchDesc *__restrict__ desc, const long long *__restrict
     Batch<VT, 1, U> B;
     load_batch<VT, 1, U>(B, cols + base, vals + base, 32LL, 0, info.w, true);
     const RowEnds rm(tm, info.x, info.y, lane);
-    const AT sum = chunk_sum<32, VT, AT, 1>(cols, vals, x, base, info.w, rm.owns, B);
+    const AT sum = chunk_sum<32, VT, AT, 1>(cols, vals, xg, base, info.w, rm.owns, B);
     reduce_store<0, AT>(sum, rm, info.x, lane, ep, y);
+}
+
+// Every group of a batch of matrices (k = 1, V = 1): one block of 32 warps
+// per matrix, the matrices with the most slots first (`order`), the
+// matrix's groups shared out among the warps.  When the matrix's x fits the
+// block's shared memory (at most xCap elements) it is copied there once and
+// gathered from there: a warp's 32 random shared-memory reads cost a few
+// bank wavefronts, where 32 random global reads cost 32 L1 wavefronts even
+// when they hit, and those wavefronts are what bounds a product whose x
+// stays on chip.  Larger members gather from global memory.
+template <typename VT, typename AT>
+__global__ void __launch_bounds__(1024, sizeof(AT) == 4 ? 2 : 1)
+k_batch_spmv_g32(const BatchDesc *__restrict__ desc, const int *__restrict__ order, int xCap,
+                 const AT *__restrict__ X, AT *__restrict__ Y) {
+    extern __shared__ __align__(16) unsigned char xsm[];
+    const int m = __ldg(order + blockIdx.x);
+    const BatchDesc d = desc[m];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const AT *x = X + d.colBase;
+    AT *y = Y + d.rowBase;
+    const VT *vals = static_cast<const VT *>(d.vals);
+    if (d.nCols <= xCap) {   // block-uniform
+        AT *xs = reinterpret_cast<AT *>(xsm);
+        for (int i = threadIdx.x; i < d.nCols; i += 1024) xs[i] = __ldg(x + i);
+        __syncthreads();
+        const XShared<AT> xg{(unsigned)__cvta_generic_to_shared(xsm)};
+        for (long long g = warp; g < d.nGroups; g += 32)
+            batch_group<VT, AT>(__ldg(d.gi + g), d.tm, d.cols, vals, xg, y, lane);
+    } else {
+        const XGlobal<AT> xg{x};
+        for (long long g = warp; g < d.nGroups; g += 32)
+            batch_group<VT, AT>(__ldg(d.gi + g), d.tm, d.cols, vals, xg, y, lane);
+    }
 }
 
 // Roofline probe: the memory accesses of k_spmv_g32 (G = 32, V = 1) without
@@ -517,29 +548,45 @@ argcsr_status launch_probe_gather(const argcsr_matrix *A, const void *x, int mod
     return ARGCSR_OK;
 }
 
-argcsr_status launch_batch_spmv(const BatchDesc *desc, const long long *groupPrefix, int nMat,
+// Shared memory a k_batch_spmv_g32 block may give x: two blocks per SM.
+constexpr int kBatchXBytes = 100 * 1024;
+
+template <typename VT, typename AT>
+argcsr_status launch_batch_spmv_t(const BatchDesc *desc, const int *order, int count, int maxCols,
+                                  const void *X, void *Y, cudaStream_t s) {
+    const int xCap = std::min(maxCols, kBatchXBytes / (int)sizeof(AT));
+    const size_t smem = (size_t)std::max(xCap, 1) * sizeof(AT);
+    k_batch_spmv_g32<VT, AT><<<(unsigned)count, 1024, smem, s>>>(desc, order, xCap, static_cast<const AT *>(X),
+                                                                 static_cast<AT *>(Y));
+    return ARGCSR_OK;
+}
+
+// The shared-memory limit of k_batch_spmv_g32, set once per device when a
+// batch is created (never inside a stream capture).
+argcsr_status prepare_batch_spmv() {
+    cudaError_t e = cudaFuncSetAttribute(k_batch_spmv_g32<double, double>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchXBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_batch_spmv_g32<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kBatchXBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_batch_spmv_g32<uint16_t, float>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchXBytes);
+    return e == cudaSuccess ? ARGCSR_OK : record_cuda(e, "cudaFuncSetAttribute(k_batch_spmv_g32)");
+}
+
+argcsr_status launch_batch_spmv(const BatchDesc *desc, const int *order, int count, int maxCols,
                                 long long totalGroups, argcsr_dtype dtype, const void *X, void *Y,
                                 cudaStream_t s) {
     if (totalGroups == 0) return ARGCSR_OK;
-    const unsigned blocks = (unsigned)((totalGroups + 7) / 8);
     TraceScope t("k_batch_spmv_g32", s);
+    argcsr_status st;
     switch (dtype) {
-        case ARGCSR_F64:
-            k_batch_spmv_g32<double, double><<<blocks, 256, 0, s>>>(desc, groupPrefix, nMat, totalGroups,
-                                                                   static_cast<const double *>(X),
-                                                                   static_cast<double *>(Y));
-            break;
-        case ARGCSR_F32:
-            k_batch_spmv_g32<float, float><<<blocks, 256, 0, s>>>(desc, groupPrefix, nMat, totalGroups,
-                                                                 static_cast<const float *>(X),
-                                                                 static_cast<float *>(Y));
-            break;
-        default:
-            k_batch_spmv_g32<uint16_t, float><<<blocks, 256, 0, s>>>(desc, groupPrefix, nMat, totalGroups,
-                                                                    static_cast<const float *>(X),
-                                                                    static_cast<float *>(Y));
-            break;
+        case ARGCSR_F64: st = launch_batch_spmv_t<double, double>(desc, order, count, maxCols, X, Y, s); break;
+        case ARGCSR_F32: st = launch_batch_spmv_t<float, float>(desc, order, count, maxCols, X, Y, s); break;
+        default: st = launch_batch_spmv_t<uint16_t, float>(desc, order, count, maxCols, X, Y, s); break;
     }
+    if (st != ARGCSR_OK) return st;
     count_launches(1);
     ARGCSR_CHECK_LAUNCH("k_batch_spmv_g32");
     return ARGCSR_OK;

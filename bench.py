@@ -1430,8 +1430,8 @@ def run_ncu_case(which, ncu_d=None):
     """A short, untimed launch sequence for ncu captures: for each matrix, one
     conversion (k_tile_prepare, k_resolve, k_groups, k_tile_scan, k_fill) and
     two SpMVs.  'bench' uses the bench's two matrices; 'small' a 1,000,000-row
-    lognormal matrix (D 4) and the 128^3 Laplacian (D 8) -- larger than L2,
-    about 1 GB on the device."""
+    lognormal matrix and the 128^3 Laplacian (D 8 both) -- larger than L2,
+    about 1 GB on the device; 'spmv_step' the default line's timed region."""
     import torch
     from paper_1203_5737_gb300 import argcsr as api
     from paper_1203_5737_gb300 import build
@@ -1479,6 +1479,31 @@ def run_ncu_case(which, ncu_d=None):
             api.argcsr_destroy(h, s)
         print(f"ncu case {which}: ok")
         return
+    if which == "spmv_step":
+        # the default line's timed region: both matrices converted (G 32, D
+        # per --ncu-d), 3 warm-up steps, then 2 steps, a step being the SpMV
+        # of each matrix -- 10 conversion launches, then 10 SpMV launches
+        Ds = dict(FALLBACK_D)
+        for item in filter(None, (ncu_d or "").split(",")):
+            k, v = item.split("=")
+            Ds[k] = int(v)
+        hs = []
+        for name in MATRICES:
+            A, x = synth.workload(name)
+            t = (torch.from_numpy(A.rowPointers).cuda(), torch.from_numpy(A.columns).cuda(),
+                 torch.from_numpy(A.values).cuda(), torch.from_numpy(x).cuda(),
+                 torch.empty(A.n_rows, dtype=torch.float64, device="cuda"))
+            h = api.argcsr_create_from_csr(A.n_rows, A.n_cols, A.nnz, t[0].data_ptr(), t[1].data_ptr(),
+                                           t[2].data_ptr(), api.ARGCSR_F64, GROUP_SIZE, Ds[name], 1, s)
+            hs.append((h, t))
+        for _ in range(5):
+            for h, t in hs:
+                api.argcsr_spmv(h, t[3].data_ptr(), t[4].data_ptr(), s)
+        torch.cuda.synchronize()
+        for h, _ in hs:
+            api.argcsr_destroy(h, s)
+        print(f"ncu case {which}: ok")
+        return
     if which == "bench":
         Ds = dict(FALLBACK_D)
         for item in filter(None, (ncu_d or "").split(",")):
@@ -1486,7 +1511,7 @@ def run_ncu_case(which, ncu_d=None):
             Ds[k] = int(v)
         mats = [(synth.workload(name)[0], Ds[name]) for name in MATRICES]
     else:
-        mats = [(synth.laplacian_3d(128), 8), (synth.lognormal_rows(1_000_000), 4)]
+        mats = [(synth.lognormal_rows(1_000_000), 8), (synth.laplacian_3d(128), 8)]
     for A, D in mats:
         rp = torch.from_numpy(A.rowPointers).cuda()
         cols = torch.from_numpy(A.columns).cuda()
@@ -1512,7 +1537,7 @@ def main(argv=None):
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-sweep", action="store_true", help="skip the desiredChunkSize sweep")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    p.add_argument("--ncu-case", choices=("small", "bench", "cg", "batch"),
+    p.add_argument("--ncu-case", choices=("small", "bench", "spmv_step", "cg", "batch"),
                    help="run a short untimed launch sequence for ncu, then exit")
     p.add_argument("--workload", choices=("uneven_fp64", "cg_poisson160", "batched4096", "serving"),
                    default="uneven_fp64",

@@ -28,9 +28,10 @@
 //      lists the long groups for the product; a second read-back returns
 //      the column check.
 //
-// Chunk size (Section 3, step 2).  The greedy "give one more thread to the
-// row with the greatest chunk filling until all G are placed" ends with the
-// smallest C for which sum over rows of max(1, ceil(len/C)) <= G: every
+// Chunk size (Section 3, step 2).  The greedy -- repeatedly hand one more
+// thread to the row whose chunks are fullest, until the G threads are used
+// -- ends with the smallest C for which sum over rows of max(1,
+// ceil(len/C)) <= G: every
 // greedy step only splits a row whose filling is above that C, so it never
 // overshoots, and it cannot stop above it because then the rows at the
 // maximum would need fewer threads than they hold.  k_groups finds that C

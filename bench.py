@@ -86,7 +86,10 @@ def kernel_bytes(kernel, n, n_cols, nnz, groups, slots):
     return {
         "k_tile_prepare": 4 * (n + 1) + n,          # rowPointers in, next-group deltas out
         "k_groups": 4 * (n + 1) + n + 4 * n + 16 * groups,
-        "k_fill": nnz * (4 + SV) + 4 * (n + 1) + 4 * n + 16 * groups * 2 + slots * (4 + SV),
+        # CSR entries, rowPointers, threadsMapping and the group scratch in;
+        # the padded slots out (the records themselves are k_order's)
+        "k_fill": nnz * (4 + SV) + 4 * (n + 1) + 4 * n + 16 * groups + slots * (4 + SV),
+        "k_order": 16 * groups * 2,
         "k_spmv_g32": spmv_bytes(n, n_cols, nnz, groups),
         "k_spmv_block": spmv_bytes(n, n_cols, nnz, groups),
     }.get(kernel, 0)
@@ -202,7 +205,8 @@ def measured_hbm_peak():
 KERNEL_SOURCES = {"k_fill": ("convert.cu", "device.cuh"),
                   "k_groups": ("convert.cu", "device.cuh"),
                   "k_tile_prepare": ("convert.cu", "device.cuh"),
-                  "k_spmv_g32": ("spmv.cu", "device.cuh")}
+                  # the conversion fixes the order in which the product takes the groups
+                  "k_spmv_g32": ("spmv.cu", "device.cuh", "convert.cu")}
 
 
 def strip_comments(text: str) -> str:

@@ -123,6 +123,10 @@ typedef struct {
  * copy into the interleaved values/columns arrays, padded with column -1 and
  * value +0.0.
  *
+ * The group records are kept on the device in execution order (by chunk
+ * size, largest first; see argcsr_device_arrays); argcsr_export returns them
+ * in row order.
+ *
  * The call synchronises `stream` twice (to size the output and to return the
  * validation status) and returns only when the handle is complete.  The
  * handle owns its device arrays (allocated from a stream-ordered pool owned
@@ -215,7 +219,7 @@ ARGCSR_API argcsr_status argcsr_info(argcsr_t A, argcsr_info_t *out);
  * argcsr_export -- copy the format's arrays to host memory (synchronous on
  * the legacy default stream after a device synchronisation).
  *   h_groupInfo       int32[4 * n_groups]: {firstRow, size, offset, chunkSize}
- *                     per group (Listing 1);
+ *                     per group (Listing 1), groups in row order;
  *   h_threadsMapping  int32[n_rows];
  *   h_columns         int32[n_slots];
  *   h_values          n_slots elements of the handle's dtype.
@@ -226,7 +230,11 @@ ARGCSR_API argcsr_status argcsr_export(argcsr_t A, int32_t *h_groupInfo,
                                        void *h_values);
 
 /* Borrow the handle's device arrays (valid until argcsr_destroy).  Any
- * output pointer may be NULL. */
+ * output pointer may be NULL.  The device copy of groupInfo holds the same
+ * records as argcsr_export in execution order -- by chunk size, largest
+ * first, so that the product's blocks get groups of equal work -- not in row
+ * order; every record names its first row, and sorting by it gives the
+ * format's order. */
 ARGCSR_API argcsr_status argcsr_device_arrays(argcsr_t A, const int32_t **d_groupInfo,
                                               const int32_t **d_threadsMapping,
                                               const int32_t **d_columns,

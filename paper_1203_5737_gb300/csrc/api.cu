@@ -4,6 +4,8 @@
 
 #include <mutex>
 
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace argcsr {
@@ -186,6 +188,14 @@ ARGCSR_API argcsr_status argcsr_export(argcsr_t A, int32_t *h_groupInfo, int32_t
         if (!c.dst || c.bytes == 0) continue;
         e = cudaMemcpy(c.dst, c.src, c.bytes, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return record_cuda(e, "argcsr_export: copy");
+    }
+    // the device keeps the group records in execution order; the format's
+    // order is by row (every record names its first row, and groups tile the
+    // rows, so sorting by it restores the order of Section 3 exactly)
+    if (h_groupInfo && A->execution_order && A->n_groups > 1) {
+        struct Rec { int32_t v[4]; };
+        Rec *r = reinterpret_cast<Rec *>(h_groupInfo);
+        std::sort(r, r + A->n_groups, [](const Rec &a, const Rec &b) { return a.v[0] < b.v[0]; });
     }
     return ARGCSR_OK;
 }

@@ -101,6 +101,15 @@ __host__ __device__ constexpr size_t groups_pfx_offset(int T, int G) {
 
 constexpr int kTileThreads = 512;   // threads of the per-tile kernels
 
+// Groups are stored in execution order: by chunk size, largest first.  The
+// product gives a block 8 (G = 32) groups and a block stays resident until
+// its slowest group is done; in row order the largest chunk size of 8
+// neighbouring groups is about 1.5 times their mean on uneven rows, so a
+// third of the warp slots would sit idle.  Bucket of a chunk size: itself up
+// to kLongChunk, one bucket above (long groups, any order among themselves).
+constexpr int kOrderBuckets = kLongChunk + 2;
+__device__ __forceinline__ int order_bucket(int C) { return C > kLongChunk ? kLongChunk + 1 : max(C, 0); }
+
 // ---------------------------------------------------------------------------
 // 1-2. Per tile: next[s] - s for every row s of the tile (and validation of
 // rowPointers), then, for every entry e < G, where the chain leaves the tile
@@ -272,7 +281,7 @@ __global__ void __launch_bounds__(kTileThreads)
 k_groups(int n, int T, int V, int onePerRow, int gallop, const int *__restrict__ rp, const uint8_t *__restrict__ delta,
          const int *__restrict__ tileEntry, const int *__restrict__ tileGroupBase,
          int4 *__restrict__ gscratch, int *__restrict__ threadsMapping,
-         long long *__restrict__ tileSlots, DeviceTotals *tot) {
+         long long *__restrict__ tileSlots, int *__restrict__ hist, DeviceTotals *tot) {
     constexpr int B = subtile_rows<G>();
     const int S = T / B;
     extern __shared__ __align__(16) uint8_t smem[];
@@ -287,6 +296,8 @@ k_groups(int n, int T, int V, int onePerRow, int gallop, const int *__restrict__
     int *pfx = reinterpret_cast<int *>(smem + groups_pfx_offset(T, G));       // T + G, padded
     __shared__ int s_count;
     __shared__ long long s_warp[kTileThreads / 32];
+    __shared__ int s_hist[kOrderBuckets];
+    for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x) s_hist[i] = 0;
 
     const int k = blockIdx.x;
     const long long tbase = (long long)k * T;
@@ -398,8 +409,12 @@ k_groups(int n, int T, int V, int onePerRow, int gallop, const int *__restrict__
         gscratch[gbase + i] = make_int4(first, size | (k << 8), 0, C <= 0x7fffffffLL ? (int)C : -1);
         chunk[i] = C <= 0x7fffffffLL ? (int)C : 0x7fffffff;
         if (C > 0x7fffffffLL) flag(&tot->status, kSlotOverflow);
+        if (hist) atomicAdd(&s_hist[order_bucket(C <= 0x7fffffffLL ? (int)C : 0x7fffffff)], 1);
     }
     __syncthreads();
+    if (hist)
+        for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x)
+            if (s_hist[i]) atomicAdd(hist + i, s_hist[i]);
     // threadsMapping of the rows this tile's groups cover: from the first
     // start to the end of the last group (which may reach into the next tile)
     if (count > 0) {
@@ -441,7 +456,7 @@ k_groups(int n, int T, int V, int onePerRow, int gallop, const int *__restrict__
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024)
 k_tile_scan(int numTiles, const long long *__restrict__ tileSlots, long long *__restrict__ tileSlotBase,
-            DeviceTotals *tot) {
+            const int *__restrict__ hist, int *__restrict__ orderBase, DeviceTotals *tot) {
     __shared__ long long s_warp[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int per = (numTiles + 1023) / 1024;
@@ -465,6 +480,30 @@ k_tile_scan(int numTiles, const long long *__restrict__ tileSlots, long long *__
         for (int v = 0; v < 32; ++v) total += s_warp[v];
         tot->n_slots = total;
         if (total > 0x7fffffffLL) flag(&tot->status, kSlotOverflow);
+    }
+    // first position of each chunk-size bucket in the execution order
+    // (largest chunk size first): an exclusive scan by the first warp
+    if (hist && warp == 0) {   // warp-uniform
+        constexpr int PER = (kOrderBuckets + 31) / 32;
+        int v[PER], cnt = 0;
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int e = lane * PER + u;   // position in execution order
+            v[u] = e < kOrderBuckets ? hist[kOrderBuckets - 1 - e] : 0;
+            cnt += v[u];
+        }
+        int inc = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += t;
+        }
+        int at = inc - cnt;
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int e = lane * PER + u;
+            if (e < kOrderBuckets) orderBase[kOrderBuckets - 1 - e] = at;
+            at += v[u];
+        }
     }
 }
 
@@ -536,7 +575,8 @@ __device__ __forceinline__ void copy_chunk(const int *__restrict__ cIn, const VT
     }
 }
 
-// G = 32: one warp per group.  A group's loads form two dependent rounds:
+// G = 32: one warp per group (the group records are written by k_order).
+// A group's loads form two dependent rounds:
 // its slot base, threadsMapping words and row pointers (lane l reads those
 // of row l; the bounds of the row a chunk belongs to come by shuffle), then
 // its entries.  The record of the warp's next group is loaded one group
@@ -547,7 +587,7 @@ __device__ __forceinline__ void fill_g32(long long nGroups, int n_cols, const lo
                                          const int *__restrict__ colsIn, const VT *__restrict__ valsIn,
                                          const int *__restrict__ threadsMapping, int4 *__restrict__ groupInfo,
                                          int *__restrict__ colsOut, VO *__restrict__ valsOut,
-                                         int *__restrict__ longList, long long longCap, DeviceTotals *tot) {
+                                         DeviceTotals *tot) {
     const int lane = threadIdx.x & 31;
     const long long W = (long long)gridDim.x * (blockDim.x >> 5);
     long long t = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -565,13 +605,6 @@ __device__ __forceinline__ void fill_g32(long long nGroups, int n_cols, const lo
         const int end = lane < size ? threadsMapping[first + lane] : 0;
         const int rowStart = lane < size ? rp[first + lane] : 0;
         const int lastEnd = rp[first + size];
-        if (lane == 0) {
-            groupInfo[g] = make_int4(first, size, off, C);
-            if (longList && C > kLongChunk) {
-                const long long i = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&tot->n_long), 1ull);
-                if (i < longCap) longList[i] = (int)g;
-            }
-        }
         if (C <= 0) continue;   // warp-uniform
         // row ends as a bit mask: the row of chunk `lane` is the number of
         // ends below it, its first chunk follows the previous end
@@ -598,10 +631,10 @@ k_fill(long long nGroups, int n_cols, const long long *__restrict__ tileSlotBase
        const int4 *__restrict__ gscratch, const int *__restrict__ rp, const int *__restrict__ colsIn,
        const VT *__restrict__ valsIn, const int *__restrict__ threadsMapping,
        int4 *__restrict__ groupInfo, int *__restrict__ colsOut, VO *__restrict__ valsOut,
-       int *__restrict__ longList, long long longCap, DeviceTotals *tot) {
+       DeviceTotals *tot) {
     if constexpr (G == 32) {
         fill_g32<VT, VO, V>(nGroups, n_cols, tileSlotBase, gscratch, rp, colsIn, valsIn, threadsMapping,
-                            groupInfo, colsOut, valsOut, longList, longCap, tot);
+                            groupInfo, colsOut, valsOut, tot);
     } else {
         // G = 64 or 128: one group per warp; the row of each chunk from a
         // per-warp table built from threadsMapping
@@ -613,7 +646,6 @@ k_fill(long long nGroups, int n_cols, const long long *__restrict__ tileSlotBase
             const int4 s = gscratch[g];
             const int first = s.x, size = s.y & 255, C = s.w;
             const long long off = tileSlotBase[s.y >> 8] + s.z;
-            if (lane == 0) groupInfo[g] = make_int4(first, size, (int)off, C);
             if (C <= 0) continue;
             for (int c = lane; c < G; c += 32) s_rowOf[warp][c] = -1;
             __syncwarp();
@@ -646,6 +678,45 @@ k_fill(long long nGroups, int n_cols, const long long *__restrict__ tileSlotBase
     }
 }
 
+// The group records (Listing 1) from the structure pass, one thread per
+// group: its slot offset completed with its tile's base, placed in
+// execution order (largest chunk size first; orderCursor holds each
+// sub-bucket's first position and hands positions out) or, without
+// orderCursor, in row order.  The long groups (G = 32, V = 1) are listed by
+// their position for the product.
+__global__ void __launch_bounds__(256)
+k_order(long long nGroups, const long long *__restrict__ tileSlotBase, const int4 *__restrict__ gscratch,
+        int4 *__restrict__ groupInfo, int *__restrict__ orderCursor, int *__restrict__ longList,
+        long long longCap, DeviceTotals *tot) {
+    // positions are handed out per block: ranks inside the block from
+    // shared-memory counters, then one global reservation per bucket the
+    // block uses
+    __shared__ int s_cnt[kOrderBuckets], s_base[kOrderBuckets];
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool on = g < nGroups;
+    const int4 s = on ? gscratch[g] : make_int4(0, 0, 0, 0);
+    const int size = s.y & 255, C = s.w;
+    long long pos = g;
+    if (orderCursor) {   // block-uniform
+        for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x) s_cnt[i] = 0;
+        __syncthreads();
+        const int b = order_bucket(C);
+        const int r = on ? atomicAdd(&s_cnt[b], 1) : 0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < kOrderBuckets; i += blockDim.x)
+            if (s_cnt[i]) s_base[i] = atomicAdd(orderCursor + i, s_cnt[i]);
+        __syncthreads();
+        pos = s_base[b] + r;
+    }
+    if (!on) return;
+    const int off = (int)(tileSlotBase[s.y >> 8] + s.z);
+    groupInfo[pos] = make_int4(s.x, size, off, C);
+    if (longList && C > kLongChunk) {
+        const long long i = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&tot->n_long), 1ull);
+        if (i < longCap) longList[i] = (int)pos;
+    }
+}
+
 // Dynamic shared memory of k_groups: delta (T), starts (2T), chunk sizes
 // (4T), row lengths (4(T+G), padded), sub-tile tables (2 S G), sub-tile
 // entries and bases (4 S), threadsMapping of the tile's rows (4(T+G), padded).
@@ -667,8 +738,8 @@ struct Kernels {
     static argcsr_status run_structure(int n, long long nnz, long long limit, int T, int numTiles,
                                        int V, int onePerRow, const int *rp, uint8_t *delta, uint8_t *fn, int *cnt,
                                        int *tileEntry, int *tileGroupBase, int4 *gscratch, int *tm,
-                                       long long *tileSlots, long long *tileSlotBase,
-                                       DeviceTotals *tot, cudaStream_t s) {
+                                       long long *tileSlots, long long *tileSlotBase, int *hist,
+                                       int *orderBase, DeviceTotals *tot, cudaStream_t s) {
         {
             TraceScope t("k_tile_prepare", s);
             k_tile_prepare<G><<<numTiles, kTileThreads, prepare_smem(T, G), s>>>(n, nnz, T, limit, rp, delta,
@@ -682,11 +753,11 @@ struct Kernels {
             TraceScope t("k_groups", s);
             const size_t smem = groups_smem(T, G);
             k_groups<G><<<numTiles, kTileThreads, smem, s>>>(n, T, V, onePerRow, limit <= 6LL * G ? 1 : 0, rp, delta, tileEntry, tileGroupBase,
-                                                     gscratch, tm, tileSlots, tot);
+                                                     gscratch, tm, tileSlots, hist, tot);
         }
         {
             TraceScope t("k_tile_scan", s);
-            k_tile_scan<<<1, 1024, 0, s>>>(numTiles, tileSlots, tileSlotBase, tot);
+            k_tile_scan<<<1, 1024, 0, s>>>(numTiles, tileSlots, tileSlotBase, hist, orderBase, tot);
         }
         count_launches(4);
         ARGCSR_CHECK_LAUNCH("conversion structure kernels");
@@ -697,25 +768,28 @@ struct Kernels {
                                   const long long *tileSlotBase,
                                   const int4 *gscratch, const int *rp, const int *cols,
                                   const void *vals, const int *tm, int4 *gi, int *colsOut,
-                                  void *valsOut, int *longList, long long longCap, DeviceTotals *tot,
-                                  cudaStream_t s) {
+                                  void *valsOut, int *longList, long long longCap, int *orderCursor,
+                                  DeviceTotals *tot, cudaStream_t s) {
         if (nGroups == 0) return ARGCSR_OK;
+        {
+            TraceScope t("k_order", s);
+            k_order<<<(unsigned)((nGroups + 255) / 256), 256, 0, s>>>(nGroups, tileSlotBase, gscratch, gi,
+                                                                    orderCursor, longList, longCap, tot);
+            count_launches(1);
+        }
         const long long blocks = min((nGroups + 7) / 8, 152LL * 64);
         TraceScope t("k_fill", s);
         const VT *v = static_cast<const VT *>(vals);
         VO *vo = static_cast<VO *>(valsOut);
         if (V == 1)
             k_fill<G, VT, VO, 1><<<(unsigned)blocks, 256, 0, s>>>(nGroups, n_cols, tileSlotBase, gscratch, rp,
-                                                                  cols, v, tm, gi, colsOut, vo, longList,
-                                                                  longCap, tot);
+                                                                  cols, v, tm, gi, colsOut, vo, tot);
         else if (V == 2)
             k_fill<G, VT, VO, 2><<<(unsigned)blocks, 256, 0, s>>>(nGroups, n_cols, tileSlotBase, gscratch, rp,
-                                                                  cols, v, tm, gi, colsOut, vo, nullptr, 0,
-                                                                  tot);
+                                                                  cols, v, tm, gi, colsOut, vo, tot);
         else
             k_fill<G, VT, VO, 4><<<(unsigned)blocks, 256, 0, s>>>(nGroups, n_cols, tileSlotBase, gscratch, rp,
-                                                                  cols, v, tm, gi, colsOut, vo, nullptr, 0,
-                                                                  tot);
+                                                                  cols, v, tm, gi, colsOut, vo, tot);
         count_launches(1);
         ARGCSR_CHECK_LAUNCH("k_fill");
         return ARGCSR_OK;
@@ -760,7 +834,7 @@ struct PinnedTotals {
 };
 
 struct Scratch {
-    void *p[9] = {};
+    void *p[10] = {};
     cudaStream_t s;
     ~Scratch() { for (void *q : p) pool_free(q, s); }
 };
@@ -834,6 +908,7 @@ extern "C" ARGCSR_API argcsr_status argcsr_create_from_csr_as(
     ALLOC(6, (size_t)numTiles * 8);                        // tileSlots
     ALLOC(7, (size_t)numTiles * 8);                        // tileSlotBase
     ALLOC(8, sizeof(DeviceTotals));
+    ALLOC(9, 2 * kOrderBuckets * sizeof(int));            // chunk-size histogram, bucket cursors
     if ((st = pool_alloc((void **)&A->d_threadsMapping, (size_t)n * 4, s)) != ARGCSR_OK) return fail(st);
 #undef ALLOC
     uint8_t *delta = (uint8_t *)sc.p[0];
@@ -842,14 +917,17 @@ extern "C" ARGCSR_API argcsr_status argcsr_create_from_csr_as(
     int4 *gscratch = (int4 *)sc.p[5];
     long long *tileSlots = (long long *)sc.p[6], *tileSlotBase = (long long *)sc.p[7];
     DeviceTotals *tot = (DeviceTotals *)sc.p[8];
+    int *hist = (int *)sc.p[9], *orderBase = hist + kOrderBuckets;
 
     cudaError_t e = cudaMemsetAsync(tot, 0, sizeof(DeviceTotals), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(hist, 0, kOrderBuckets * sizeof(int), s);
     if (e != cudaSuccess) return fail(record_cuda(e, "cudaMemsetAsync"));
+    A->execution_order = 1;
     const long long limit = (long long)D * G;
     switch (G) {
-        case 32: st = set_smem_limits<32>(T); if (!st) st = Kernels<32>::run_structure(n, nnz, limit, T, numTiles, V, P1, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, A->d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
-        case 64: st = set_smem_limits<64>(T); if (!st) st = Kernels<64>::run_structure(n, nnz, limit, T, numTiles, V, P1, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, A->d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
-        default: st = set_smem_limits<128>(T); if (!st) st = Kernels<128>::run_structure(n, nnz, limit, T, numTiles, V, P1, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, A->d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
+        case 32: st = set_smem_limits<32>(T); if (!st) st = Kernels<32>::run_structure(n, nnz, limit, T, numTiles, V, P1, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, A->d_threadsMapping, tileSlots, tileSlotBase, hist, orderBase, tot, s); break;
+        case 64: st = set_smem_limits<64>(T); if (!st) st = Kernels<64>::run_structure(n, nnz, limit, T, numTiles, V, P1, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, A->d_threadsMapping, tileSlots, tileSlotBase, hist, orderBase, tot, s); break;
+        default: st = set_smem_limits<128>(T); if (!st) st = Kernels<128>::run_structure(n, nnz, limit, T, numTiles, V, P1, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, A->d_threadsMapping, tileSlots, tileSlotBase, hist, orderBase, tot, s); break;
     }
     if (st != ARGCSR_OK) return fail(st);
 
@@ -878,7 +956,7 @@ extern "C" ARGCSR_API argcsr_status argcsr_create_from_csr_as(
     Kernels<GG>::template run_fill<VI, VO>(A->n_groups, V, n_cols, tileSlotBase,                   \
                                            gscratch, d_rowPointers, d_columns, d_values,          \
                                            A->d_threadsMapping, A->d_groupInfo, A->d_columns,     \
-                                           A->d_values, A->d_longGroups, longCap, tot, s)
+                                           A->d_values, A->d_longGroups, longCap, orderBase, tot, s)
 #define FILL_G(VI, VO) (G == 32 ? FILL(32, VI, VO) : G == 64 ? FILL(64, VI, VO) : FILL(128, VI, VO))
     if (in_dtype == dtype) {
         if (es == 8) st = FILL_G(double, double);
@@ -1016,9 +1094,9 @@ extern "C" ARGCSR_API argcsr_status argcsr_convert_noalloc(
     if (e != cudaSuccess) return record_cuda(e, "cudaMemsetAsync");
     const long long limit = (long long)D * G;
     switch (G) {
-        case 32: st = set_smem_limits<32>(T); if (!st) st = Kernels<32>::run_structure(n, nnz, limit, T, numTiles, V, P1, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
-        case 64: st = set_smem_limits<64>(T); if (!st) st = Kernels<64>::run_structure(n, nnz, limit, T, numTiles, V, P1, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
-        default: st = set_smem_limits<128>(T); if (!st) st = Kernels<128>::run_structure(n, nnz, limit, T, numTiles, V, P1, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, d_threadsMapping, tileSlots, tileSlotBase, tot, s); break;
+        case 32: st = set_smem_limits<32>(T); if (!st) st = Kernels<32>::run_structure(n, nnz, limit, T, numTiles, V, P1, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, d_threadsMapping, tileSlots, tileSlotBase, nullptr, nullptr, tot, s); break;
+        case 64: st = set_smem_limits<64>(T); if (!st) st = Kernels<64>::run_structure(n, nnz, limit, T, numTiles, V, P1, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, d_threadsMapping, tileSlots, tileSlotBase, nullptr, nullptr, tot, s); break;
+        default: st = set_smem_limits<128>(T); if (!st) st = Kernels<128>::run_structure(n, nnz, limit, T, numTiles, V, P1, d_rowPointers, delta, fn, cnt, tileEntry, tileGroupBase, gscratch, d_threadsMapping, tileSlots, tileSlotBase, nullptr, nullptr, tot, s); break;
     }
     if (st != ARGCSR_OK) return st;
     // the totals come back into this stack copy: a copy into pageable
@@ -1045,7 +1123,7 @@ extern "C" ARGCSR_API argcsr_status argcsr_convert_noalloc(
     Kernels<GG>::template run_fill<VT>(h.n_groups, V, n_cols, tileSlotBase,                        \
                                        gscratch, d_rowPointers, d_columns, d_values,               \
                                        d_threadsMapping, gi, d_out_columns, d_out_values, nullptr, 0, \
-                                       tot, s)
+                                       nullptr, tot, s)
     if (es == 8) st = G == 32 ? FILL(32, double) : G == 64 ? FILL(64, double) : FILL(128, double);
     else if (es == 4) st = G == 32 ? FILL(32, float) : G == 64 ? FILL(64, float) : FILL(128, float);
     else st = G == 32 ? FILL(32, uint16_t) : G == 64 ? FILL(64, uint16_t) : FILL(128, uint16_t);

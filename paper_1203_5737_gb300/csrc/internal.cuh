@@ -42,13 +42,15 @@ struct argcsr_matrix {
     int32_t one_per_row;        // 1: every row one thread (no adaptive step)
     argcsr_dtype dtype;
     int64_t n_groups, n_slots;
-    int4 *d_groupInfo;          // {firstRow, size, offset, chunkSize}
+    int4 *d_groupInfo;          // {firstRow, size, offset, chunkSize}, in execution order
+                                // (execution_order: by chunk size, largest first) or row order
     int32_t *d_threadsMapping;  // group-local inclusive prefix of threads per row
     int32_t *d_columns;         // S slots, -1 = padding
     void *d_values;             // S slots of dtype, +0.0 = padding
     int64_t device_bytes;
-    int32_t *d_longGroups = nullptr;   // indices of the long groups (G 32, V 1)
+    int32_t *d_longGroups = nullptr;   // positions in d_groupInfo of the long groups (G 32, V 1)
     int64_t n_long = 0;
+    int32_t execution_order = 0;       // d_groupInfo records sorted by chunk size, not by row
 };
 
 namespace argcsr {

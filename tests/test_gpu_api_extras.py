@@ -174,3 +174,30 @@ def test_caller_allocator_backs_every_allocation():
     r = subprocess.run([sys.executable, "-c", script], capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-4000:]
     assert "allocator ok" in r.stdout
+
+
+class _DevView:
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (ptr, False), "version": 3}
+
+
+@pytest.mark.parametrize("G,D,V", [(32, 4, 1), (32, 8, 1), (64, 4, 2), (128, 2, 1)])
+def test_device_group_records_are_in_execution_order(G, D, V):
+    """The handle keeps the oracle's group records on the device ordered by
+    chunk size (largest first, chunk sizes above 64 together at the front);
+    the exported records are those same records in row order."""
+    A = synth.random_csr(30000, 20000, 77 + G, mean_len=9, p_empty=0.1, n_huge=5, huge_len=6000)
+    rp = torch.from_numpy(A.rowPointers).to(DEV)
+    cols = torch.from_numpy(A.columns).to(DEV)
+    with ArgCsrMatrix.from_csr(rp, cols, torch.from_numpy(A.values).to(DEV), A.n_cols, group_size=G,
+                               desired_chunk_size=D, vec_width=V) as M:
+        ng = M.info()["n_groups"]
+        gi_ptr = api.argcsr_device_arrays(M.handle)[0]
+        dev = torch.as_tensor(_DevView(gi_ptr, (ng, 4), "<i4"), device=DEV).cpu().numpy()
+        exported = M.export()["groupInfo"]
+    ref = oracle.convert(A, G, D, V)
+    assert np.array_equal(exported, ref.groupInfo)
+    assert np.array_equal(dev[np.argsort(dev[:, 0], kind="stable")], ref.groupInfo)
+    C = dev[:, 3]
+    bucket = np.where(C > 64, 65, C)
+    assert np.all(np.diff(bucket) <= 0)

@@ -57,7 +57,8 @@ WORKLOAD = ("uneven rows FP64: lognormal(2.3,1.2) n=2,000,000 + 3D 7-point Lapla
             "ARG-CSR (G=32, D autotuned per matrix) resident in HBM; step = SpMV of both")
 GROUP_SIZE = 32
 MATRICES = ("lognormal_2m", "laplace3d_128")
-FALLBACK_D = {"lognormal_2m": 8, "laplace3d_128": 8}
+FALLBACK_D = {"lognormal_2m": 8, "laplace3d_128": 8}   # what the autotuner picks on GB300
+FALLBACK_V = {"lognormal_2m": 2, "laplace3d_128": 1}
 SV = 8   # bytes per stored value (FP64)
 SX = 8   # bytes per x / y element
 FALLBACK_HBM_GBS = 6800.0
@@ -361,24 +362,24 @@ def run_ours(args):
     peak, peak_kind = measured_hbm_peak()
     mats = [prepare(name, dev, torch) for name in MATRICES]
 
-    def convert(m, D, storage=None, src=None, **kw):
+    def convert(m, D, storage=None, src=None, V=1, **kw):
         rp, cols, vals = src or (m.rp, m.cols, m.vals)
         if storage is None:
             return api.argcsr_create_from_csr(m.n, m.n_cols, m.nnz, rp.data_ptr(), cols.data_ptr(),
-                                              vals.data_ptr(), api.ARGCSR_F64, GROUP_SIZE, D, 1, s, **kw)
+                                              vals.data_ptr(), api.ARGCSR_F64, GROUP_SIZE, D, V, s, **kw)
         return api.argcsr_create_from_csr_as(m.n, m.n_cols, m.nnz, rp.data_ptr(), cols.data_ptr(),
-                                             vals.data_ptr(), api.ARGCSR_F64, storage, GROUP_SIZE, D, 1, s)
+                                             vals.data_ptr(), api.ARGCSR_F64, storage, GROUP_SIZE, D, V, s)
 
     # desiredChunkSize per matrix from the library's autotuner (G = 32, the
     # paper's candidates of D); untimed set-up, like the conversion itself
     for m in mats:
         if args.no_autotune:
-            m.D, m.tune_us = FALLBACK_D[m.name], None
+            m.D, m.V, m.tune_us = FALLBACK_D[m.name], FALLBACK_V[m.name], None
         else:
-            (G, m.D, _, _), m.tune_us = api.argcsr_autotune(
+            (G, m.D, m.V, _), m.tune_us = api.argcsr_autotune(
                 m.n, m.n_cols, m.nnz, m.rp.data_ptr(), m.cols.data_ptr(), m.vals.data_ptr(),
-                api.ARGCSR_F64, 1, 1, 10, s)
-        m.h = convert(m, m.D)
+                api.ARGCSR_F64, 1, 1 | 16, 10, s)
+        m.h = convert(m, m.D, V=m.V)
         info = api.argcsr_info(m.h)
         m.groups, m.slots = info.n_groups, info.n_slots
         m.spmv_bytes = spmv_bytes(m.n, m.n_cols, m.nnz, m.groups)
@@ -429,7 +430,7 @@ def run_ours(args):
         pr = {f"mode{md}": round(_time_us(torch, stream, lambda: api.argcsr_probe_gather(m.h, xp, md, s),
                                           reps), 2) for md in (0, 1, 2)}
         probe[m.name] = pr
-        spmv[m.name] = {"D": m.D, "us": round(m.us, 2), "gbs": round(_gbs(m.spmv_bytes, m.us), 1),
+        spmv[m.name] = {"D": m.D, "V": m.V, "us": round(m.us, 2), "gbs": round(_gbs(m.spmv_bytes, m.us), 1),
                         "frac": round(_gbs(m.spmv_bytes, m.us) / peak, 4),
                         "gflops": round(2 * m.nnz / (m.us * 1e-6) / 1e9, 1),
                         "groups": m.groups, "slots_per_nnz": round(m.slots / m.nnz, 4),
@@ -457,7 +458,7 @@ def run_ours(args):
     # freed (the conversion is informational: the paper does not time it)
     def conv_step():
         for m in mats:
-            h = convert(m, m.D)
+            h = convert(m, m.D, V=m.V)
             api.argcsr_spmv(h, m.x.data_ptr(), m.y.data_ptr(), s)
             api.argcsr_destroy(h, s)
 
@@ -537,7 +538,7 @@ def run_ours(args):
         yd = torch.empty(m.n, dtype=torch.float32, device=dev)
         res = {}
         for name, code in (("f32", api.ARGCSR_F32), ("bf16", api.ARGCSR_BF16)):
-            h = convert(m, m.D, storage=code)
+            h = convert(m, m.D, storage=code, V=m.V)
             info = api.argcsr_info(h)
             nb = spmv_bytes(m.n, m.n_cols, m.nnz, info.n_groups, sv=DTYPE_BYTES[code], sx=4)
             us = _time_us(torch, stream, lambda: api.argcsr_spmv(h, xd.data_ptr(), yd.data_ptr(), s), reps)
@@ -686,7 +687,7 @@ def run_ours(args):
                 ready.append(ev)
         for m, ev in zip(mats, ready):
             stream.wait_event(ev)
-            h = convert(m, m.D)
+            h = convert(m, m.D, V=m.V)
             api.argcsr_spmv(h, m.x.data_ptr(), m.y.data_ptr(), s)
             api.argcsr_destroy(h, s)
             m.h_y.copy_(m.y, non_blocking=True)
@@ -726,7 +727,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(seconds=args.cpu_seconds, Ds={k: v["D"] for k, v in spmv.items()})
+        cpu = cpu_baseline(seconds=args.cpu_seconds, Ds={k: (v["D"], v["V"]) for k, v in spmv.items()})
 
     if rank == 0:
         line = {
@@ -736,6 +737,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "group_size": GROUP_SIZE,
                        "desired_chunk_size": {k: v["D"] for k, v in spmv.items()},
+                       "vec_width": {k: v["V"] for k, v in spmv.items()},
                        "n_rows": {"lognormal_2m": 2000000, "laplace3d_128": 128 ** 3},
                        "bytes_per_step": step_bytes,
                        "l2": f"inputs larger than L2 ({step_bytes / 2**20:.0f} MiB per step "
@@ -785,14 +787,15 @@ class OracleWork:
     in parallel with unchanged arithmetic."""
 
     def __init__(self, inputs, threads):
-        """inputs: (name, A, x, D) per matrix."""
+        """inputs: (name, A, x, D or (D, V)) per matrix."""
         import oracle
         oracle.build()
         self.oracle = oracle
         self.threads = max(1, threads)
         self.items = []
-        for name, A, x, D in inputs:
-            M = oracle.convert(A, GROUP_SIZE, D)
+        for name, A, x, DV in inputs:
+            D, V = DV if isinstance(DV, tuple) else (DV, 1)
+            M = oracle.convert(A, GROUP_SIZE, D, V)
             y = np.zeros(A.n_rows, dtype=np.float64)
             slots = M.groupInfo[:, 2].astype(np.int64)
             g_cuts = np.searchsorted(slots, np.linspace(0, M.n_slots, self.threads + 1)[1:-1])
@@ -807,7 +810,7 @@ class OracleWork:
                                             (A.rowPointers[r0:r1 + 1] - a).astype(np.int32),
                                             A.columns[a:b], A.values[a:b], name))
             self.items.append({"name": name, "A": A, "M": M, "x": np.ascontiguousarray(x), "y": y,
-                               "D": D, "g_cuts": g_cuts, "csr_slices": csr_slices,
+                               "D": D, "V": V, "g_cuts": g_cuts, "csr_slices": csr_slices,
                                "bytes": spmv_bytes(A.n_rows, A.n_cols, A.nnz, M.n_groups),
                                "csr_bytes": csr_spmv_bytes(A.n_rows, A.n_cols, A.nnz)})
 
@@ -859,12 +862,12 @@ class OracleWork:
 
 
 def bench_inputs(Ds=None):
-    """(name, A, x, D) of the bench matrices, D as given or the default."""
+    """(name, A, x, (D, V)) of the bench matrices, (D, V) as given or the default."""
     Ds = Ds or {}
     out = []
     for name in MATRICES:
         A, x = synth.workload(name)
-        out.append((name, A, x, Ds.get(name, FALLBACK_D[name])))
+        out.append((name, A, x, Ds.get(name, (FALLBACK_D[name], FALLBACK_V[name]))))
     return out
 
 
@@ -914,6 +917,7 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "group_size": GROUP_SIZE,
                    "desired_chunk_size": {it["name"]: it["D"] for it in w.items},
+                   "vec_width": {it["name"]: it["V"] for it in w.items},
                    "parallelism": f"host, {threads} threads"},
         "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
                          "sample": "each step: the oracle's ARG-CSR SpMV of both matrices at full "
@@ -1488,9 +1492,11 @@ def run_ncu_case(which, ncu_d=None):
         # per --ncu-d), 3 warm-up steps, then 2 steps, a step being the SpMV
         # of each matrix -- 10 conversion launches, then 10 SpMV launches
         Ds = dict(FALLBACK_D)
+        Vs = {}
         for item in filter(None, (ncu_d or "").split(",")):
             k, v = item.split("=")
-            Ds[k] = int(v)
+            Ds[k] = int(v.split(":")[0])
+            Vs[k] = int(v.split(":")[1]) if ":" in v else 1
         hs = []
         for name in MATRICES:
             A, x = synth.workload(name)
@@ -1498,7 +1504,8 @@ def run_ncu_case(which, ncu_d=None):
                  torch.from_numpy(A.values).cuda(), torch.from_numpy(x).cuda(),
                  torch.empty(A.n_rows, dtype=torch.float64, device="cuda"))
             h = api.argcsr_create_from_csr(A.n_rows, A.n_cols, A.nnz, t[0].data_ptr(), t[1].data_ptr(),
-                                           t[2].data_ptr(), api.ARGCSR_F64, GROUP_SIZE, Ds[name], 1, s)
+                                           t[2].data_ptr(), api.ARGCSR_F64, GROUP_SIZE, Ds[name],
+                                           Vs.get(name, 1), s)
             hs.append((h, t))
         for _ in range(5):
             for h, t in hs:
@@ -1510,20 +1517,22 @@ def run_ncu_case(which, ncu_d=None):
         return
     if which == "bench":
         Ds = dict(FALLBACK_D)
+        Vs = {}
         for item in filter(None, (ncu_d or "").split(",")):
             k, v = item.split("=")
-            Ds[k] = int(v)
-        mats = [(synth.workload(name)[0], Ds[name]) for name in MATRICES]
+            Ds[k] = int(v.split(":")[0])
+            Vs[k] = int(v.split(":")[1]) if ":" in v else 1
+        mats = [(synth.workload(name)[0], Ds[name], Vs.get(name, 1)) for name in MATRICES]
     else:
-        mats = [(synth.lognormal_rows(1_000_000), 8), (synth.laplacian_3d(128), 8)]
-    for A, D in mats:
+        mats = [(synth.lognormal_rows(1_000_000), 8, 2), (synth.laplacian_3d(128), 8, 1)]
+    for A, D, V in mats:
         rp = torch.from_numpy(A.rowPointers).cuda()
         cols = torch.from_numpy(A.columns).cuda()
         vals = torch.from_numpy(A.values).cuda()
         x = torch.rand(A.n_cols, dtype=torch.float64, device="cuda")
         y = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
         h = api.argcsr_create_from_csr(A.n_rows, A.n_cols, A.nnz, rp.data_ptr(), cols.data_ptr(),
-                                       vals.data_ptr(), api.ARGCSR_F64, GROUP_SIZE, D, 1, s)
+                                       vals.data_ptr(), api.ARGCSR_F64, GROUP_SIZE, D, V, s)
         for _ in range(2):
             api.argcsr_spmv(h, x.data_ptr(), y.data_ptr(), s)
         torch.cuda.synchronize()
@@ -1549,8 +1558,8 @@ def main(argv=None):
                         "mixed-precision CG with FP64 refinement; batched4096: multi-RHS "
                         "products of 4096 matrices in one graph launch; serving: SpMV and "
                         "CG requests on a 64-matrix pool through the serving engine")
-    p.add_argument("--ncu-d", help="--ncu-case bench: desiredChunkSize per matrix, "
-                                   "e.g. lognormal_2m=8,laplace3d_128=16")
+    p.add_argument("--ncu-d", help="--ncu-case bench / spmv_step: desiredChunkSize[:vec_width] per "
+                                   "matrix, e.g. lognormal_2m=8:2,laplace3d_128=8")
     p.add_argument("--no-serving", action="store_true", help="leave the serving block out")
     p.add_argument("--no-cg", action="store_true", help="leave the CG block out")
     p.add_argument("--no-autotune", action="store_true",

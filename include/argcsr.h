@@ -185,7 +185,8 @@ ARGCSR_API argcsr_status argcsr_spmv_axpby(argcsr_t A, double alpha, const void 
  *   (mode >> 2) & 3: the gather's load instruction: 0 read-only path,
  *                    1 read-only without L1 allocation, 2 L2 only,
  *                    3 default caching load
- * Only G = 32, V = 1, ARGCSR_F64 handles (ARGCSR_ENOTSUP otherwise);
+ * Only G = 32, ARGCSR_F64 handles with V in {1, 2} (ARGCSR_ENOTSUP
+ * otherwise);
  * other modes return ARGCSR_EINVAL.  d_x as in argcsr_spmv.  Writes no
  * caller memory.  Asynchronous on `stream`; one kernel.
  * ------------------------------------------------------------------------ */
@@ -296,7 +297,8 @@ ARGCSR_API argcsr_status argcsr_batch_destroy(argcsr_batch_t batch, argcsr_strea
  * ones small) and uses 128 threads per block; this call converts the CSR
  * input with every candidate (G in the bits of group_size_mask: 1 = 32,
  * 2 = 64, 4 = 128; bit 8 adds the one-thread-per-row layouts of each G;
- * D in {1, 2, 3, 4, 6, 8, 12, 16, 32}; V = 1), times
+ * D in {1, 2, 3, 4, 6, 8, 12, 16, 32}; V = 1, and V = 2 as well when bit
+ * 16 is set), times
  * `reps` products with k right-hand sides, and returns the fastest in *best
  * (its time per product in *best_us).  Candidates whose layout has the same
  * size as one already timed are skipped.  Synchronous on `stream`.

@@ -744,11 +744,13 @@ ARGCSR_API argcsr_status argcsr_autotune(int32_t n_rows, int32_t n_cols, int64_t
     float bestT = INFINITY;
     argcsr_params bp{32, 1, 1, 0};
     const int modes = (group_size_mask & 8) ? 2 : 1;
+    const int widths = (group_size_mask & 16) ? 2 : 1;   // bit 16: V = 2 as well
     for (int gi = 0; gi < 3 && st == ARGCSR_OK; ++gi) {
         if (!(group_size_mask & (1 << gi))) continue;
         for (int mode = 0; mode < modes; ++mode)
+        for (int vw = 1; vw <= widths; ++vw)
         for (int D : Ds) {
-            argcsr_params p{Gs[gi], D, 1, mode};
+            argcsr_params p{Gs[gi], D, vw, mode};
             argcsr_t A = nullptr;
             argcsr_status cs = argcsr_create_from_csr(n_rows, n_cols, nnz, d_rowPointers, d_columns,
                                                       d_values, dtype, &p, stream, &A);

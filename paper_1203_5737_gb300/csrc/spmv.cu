@@ -485,50 +485,53 @@ k_batch_spmv_g32(const BatchDesc *__restrict__ desc, const int *__restrict__ ord
 // be dropped.  No FP64 instruction is issued.
 __device__ unsigned long long g_probe_sink;
 
-template <int MODE, int OP>
+template <int MODE, int OP, int V>
 __global__ void __launch_bounds__(256, 8)
 k_probe_g32(long long nGroups, const int4 *__restrict__ gi, const int *__restrict__ cols,
             const double *__restrict__ vals, const double *__restrict__ x) {
-    constexpr int U = ARGCSR_SPMV_ELEMS;
+    constexpr int U = (ARGCSR_SPMV_ELEMS + V - 1) / V;   // V-blocks per batch
     const int lane = threadIdx.x & 31;
     const long long g = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (g >= nGroups) return;   // warp-uniform
     const int4 info = __ldg(gi + g);
-    const long long base = (long long)info.z + lane;
+    const long long base = (long long)info.z + lane * V;
+    const int nb = info.w / V;
     unsigned long long acc = 0;
-    for (int j = 0; j < info.w; j += U) {
-        int c[U];
-        double v[U];
+    for (int j = 0; j < nb; j += U) {
+        int c[U][V];
+        double v[U][V];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            c[u] = -1;
-            v[u] = 0.0;
-            if (j + u < info.w) {
-                c[u] = __ldcs(cols + base + 32LL * (j + u));
-                if constexpr (MODE == 1) v[u] = __ldcs(vals + base + 32LL * (j + u));
+#pragma unroll
+            for (int e = 0; e < V; ++e) { c[u][e] = -1; v[u][e] = 0.0; }
+            if (j + u < nb) {
+                ld_stream<int, V>(cols + base + 32LL * V * (j + u), c[u]);
+                if constexpr (MODE == 1) ld_stream<double, V>(vals + base + 32LL * V * (j + u), v[u]);
             }
         }
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if constexpr (MODE == 2) {
-                acc ^= (unsigned)c[u];
-            } else if (c[u] >= 0) {
-                acc ^= (unsigned long long)__double_as_longlong(ldx<OP>(x + c[u]));
-                if constexpr (MODE == 1) acc ^= (unsigned long long)__double_as_longlong(v[u]);
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                if constexpr (MODE == 2) {
+                    acc ^= (unsigned)c[u][e];
+                } else if (c[u][e] >= 0) {
+                    acc ^= (unsigned long long)__double_as_longlong(ldx<OP>(x + c[u][e]));
+                    if constexpr (MODE == 1) acc ^= (unsigned long long)__double_as_longlong(v[u][e]);
+                }
             }
-        }
     }
     if (acc == 0x5a5a5a5a5a5a5a5aULL) g_probe_sink = acc;
 }
 
-template <int MODE>
+template <int MODE, int V>
 void launch_probe_mode(unsigned blocks, const argcsr_matrix *A, const double *x, int op, cudaStream_t s) {
     const auto *v = static_cast<const double *>(A->d_values);
     switch (op) {
-        case 0: k_probe_g32<MODE, 0><<<blocks, 256, 0, s>>>(A->n_groups, A->d_groupInfo, A->d_columns, v, x); break;
-        case 1: k_probe_g32<MODE, 1><<<blocks, 256, 0, s>>>(A->n_groups, A->d_groupInfo, A->d_columns, v, x); break;
-        case 2: k_probe_g32<MODE, 2><<<blocks, 256, 0, s>>>(A->n_groups, A->d_groupInfo, A->d_columns, v, x); break;
-        default: k_probe_g32<MODE, 3><<<blocks, 256, 0, s>>>(A->n_groups, A->d_groupInfo, A->d_columns, v, x); break;
+        case 0: k_probe_g32<MODE, 0, V><<<blocks, 256, 0, s>>>(A->n_groups, A->d_groupInfo, A->d_columns, v, x); break;
+        case 1: k_probe_g32<MODE, 1, V><<<blocks, 256, 0, s>>>(A->n_groups, A->d_groupInfo, A->d_columns, v, x); break;
+        case 2: k_probe_g32<MODE, 2, V><<<blocks, 256, 0, s>>>(A->n_groups, A->d_groupInfo, A->d_columns, v, x); break;
+        default: k_probe_g32<MODE, 3, V><<<blocks, 256, 0, s>>>(A->n_groups, A->d_groupInfo, A->d_columns, v, x); break;
     }
 }
 
@@ -540,9 +543,15 @@ argcsr_status launch_probe_gather(const argcsr_matrix *A, const void *x, int mod
     const int what = mode & 3, op = (mode >> 2) & 3;
     const double *xx = static_cast<const double *>(x);
     TraceScope t("k_probe_g32", s);
-    if (what == 0) launch_probe_mode<0>(blocks, A, xx, op, s);
-    else if (what == 1) launch_probe_mode<1>(blocks, A, xx, op, s);
-    else launch_probe_mode<2>(blocks, A, xx, op, s);
+    if (A->V == 2) {
+        if (what == 0) launch_probe_mode<0, 2>(blocks, A, xx, op, s);
+        else if (what == 1) launch_probe_mode<1, 2>(blocks, A, xx, op, s);
+        else launch_probe_mode<2, 2>(blocks, A, xx, op, s);
+    } else {
+        if (what == 0) launch_probe_mode<0, 1>(blocks, A, xx, op, s);
+        else if (what == 1) launch_probe_mode<1, 1>(blocks, A, xx, op, s);
+        else launch_probe_mode<2, 1>(blocks, A, xx, op, s);
+    }
     count_launches(1);
     ARGCSR_CHECK_LAUNCH("k_probe_g32");
     return ARGCSR_OK;

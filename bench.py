@@ -1585,7 +1585,7 @@ def main(argv=None):
                    help="requests of the default line's serving block")
     p.add_argument("--batch-count", type=int, default=4096)
     p.add_argument("--requests", type=int, default=600, help="serving: requests per saturation run")
-    p.add_argument("--serve-streams", type=int, default=8, help="serving: stream slots")
+    p.add_argument("--serve-streams", type=int, default=16, help="serving: stream slots")
     args = p.parse_args(argv)
     if args.ncu_case:
         run_ncu_case(args.ncu_case, args.ncu_d)

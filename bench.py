@@ -615,6 +615,12 @@ def run_ours(args):
             info = api.argcsr_info(h)
             nb = spmv_bytes(A.n_rows, A.n_cols, A.nnz, info.n_groups)
             us = _time_us(torch, stream, lambda: api.argcsr_spmv(h, x.data_ptr(), y.data_ptr(), s), 20, 3)
+            # the ceilings of the layout's memory accesses (the probe covers
+            # G 32, V <= 2): mode 0 columns + x gathers, 1 with the values
+            ceil = {}
+            if G == 32 and V <= 2:
+                ceil = {md: round(_time_us(torch, stream, lambda: api.argcsr_probe_gather(
+                    h, x.data_ptr(), md, s), 20, 3), 2) for md in (0, 1)}
             api.argcsr_destroy(h, s)
             cb = csr_spmv_bytes(A.n_rows, A.n_cols, A.nnz)
             vec = _time_us(torch, stream, lambda: api.argcsr_baseline_csr_spmv(
@@ -630,6 +636,10 @@ def run_ours(args):
                                "gbs": round(_gbs(nb, us), 1), "frac": round(_gbs(nb, us) / peak, 4),
                                "csr_vector_us": round(vec, 2), "cusparse_us": cus,
                                "csr_vector_gbs": round(_gbs(cb, vec), 1)}
+            if ceil:
+                families[fname].update({"V": V, "gather_ceiling_us": ceil[0], "access_ceiling_us": ceil[1],
+                                        "frac_of_gather_ceiling": round(ceil[0] / us, 4),
+                                        "frac_of_access_ceiling": round(ceil[1] / us, 4)})
             del rp, cols, vals, x, y
 
     # end to end through the public API: every step uploads x from pinned

@@ -361,7 +361,11 @@ k_groups(int n, int T, int V, int onePerRow, int gallop, const int *__restrict__
             // (the longest row gets at most the spare threads plus its own)
             unsigned lo = (unsigned)max((nnz + G - 1) / G,
                                         (long long)((maxlen + (G - size)) / (G - size + 1)));
+            // C = maxlen is feasible, and so is every C >= nnz / (G - size)
+            // when size < G: a row keeps max(1, ceil(len/C)) < len/C + 1
+            // threads, so the group needs fewer than nnz/C + size <= G
             unsigned hi = maxlen;
+            if (size < G) hi = min(hi, (unsigned)((nnz + (G - size) - 1) / (G - size)));
             lo = max(lo, 1u);
             // threads needed with chunk size c (stops once above G)
             auto need = [&](unsigned c) {
@@ -373,7 +377,7 @@ k_groups(int n, int T, int V, int onePerRow, int gallop, const int *__restrict__
                 }
                 return t;
             };
-            // hi (every row one thread) is always feasible.  When groups hold
+            // hi is feasible.  When groups hold
             // few nonzeros (small D) the answer is usually the lower bound or
             // just above it: probe lo, lo + 1, lo + 2, lo + 4, ... until
             // feasible, then bisect the last gap.  Otherwise bisect from the

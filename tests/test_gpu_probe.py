@@ -1,0 +1,111 @@
+"""argcsr_probe_gather: the product's memory accesses without its arithmetic,
+the roofline probe the bench reports its gather and access ceilings from.
+It runs on the layouts it models (G = 32, FP64, V 1 or 2), writes no caller
+memory, leaves the device usable, and refuses the layouts it does not model
+and malformed modes."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1203_5737_gb300 import argcsr as api  # noqa: E402
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1203_5737_gb300 import build
+    build.build()
+    oracle.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _handle(A, G, D, V, dtype=api.ARGCSR_F64):
+    rp = torch.from_numpy(A.rowPointers).to(DEV)
+    cols = torch.from_numpy(A.columns).to(DEV)
+    vals = torch.from_numpy(A.values).to(DEV)
+    if dtype == api.ARGCSR_F32:
+        vals = vals.float()
+    h = api.argcsr_create_from_csr(A.n_rows, A.n_cols, A.nnz, rp.data_ptr(), cols.data_ptr(),
+                                   vals.data_ptr(), dtype, G, D, V)
+    return h, (rp, cols, vals)
+
+
+def _status(fn):
+    try:
+        fn()
+    except api.ArgcsrError as e:
+        return e.status
+    return api.ARGCSR_OK
+
+
+@pytest.mark.parametrize("V", [1, 2])
+def test_probe_runs_every_mode_and_writes_nothing(V):
+    A = synth.random_csr(20000, 15000, 31, mean_len=6.0)
+    h, keep = _handle(A, 32, 8, V)
+    try:
+        assert oracle.structure(A.rowPointers, 32, 8, V)[1][:, 3].max() <= 64   # no long groups
+        x = torch.from_numpy(synth.uniform_vector(A.n_cols, 4)).to(DEV)
+        x0 = x.clone()
+        for what in (0, 1, 2):          # columns + gathers, + values, columns only
+            for op in (0, 1, 2, 3):     # the gather's load instruction
+                api.argcsr_probe_gather(h, x.data_ptr(), what | (op << 2))
+        torch.cuda.synchronize()
+        assert torch.equal(x, x0)
+        # the product on the same handle afterwards is still the oracle's
+        y = torch.empty(A.n_rows, dtype=torch.float64, device=DEV)
+        api.argcsr_spmv(h, x.data_ptr(), y.data_ptr())
+        torch.cuda.synchronize()
+        xh = x.cpu().numpy()
+        ref, scale = oracle.csr_spmv(A, xh), oracle.csr_abs_spmv(A, xh)
+        err = np.abs(y.cpu().numpy() - ref) / np.maximum(scale, 1e-300)
+        assert err.max() <= 1e-13
+    finally:
+        api.argcsr_destroy(h)
+
+
+def test_probe_refuses_layouts_it_does_not_model():
+    A = synth.random_csr(20000, 15000, 32, mean_len=8.0)
+    x = torch.from_numpy(synth.uniform_vector(A.n_cols, 5)).to(DEV)
+    for G, V, dtype in ((64, 1, api.ARGCSR_F64), (128, 2, api.ARGCSR_F64), (32, 4, api.ARGCSR_F64),
+                        (32, 1, api.ARGCSR_F32)):
+        h, keep = _handle(A, G, 8, V, dtype)
+        try:
+            assert _status(lambda: api.argcsr_probe_gather(h, x.data_ptr(), 0)) == api.ARGCSR_ENOTSUP
+        finally:
+            api.argcsr_destroy(h)
+    # long groups (chunk size above 64): V = 1 gives them whole blocks in the
+    # product, which the probe does not do; V = 2 keeps a warp per group
+    L = synth.random_csr(20000, 15000, 33, mean_len=8.0, n_huge=4, huge_len=6000)
+    xl = torch.from_numpy(synth.uniform_vector(L.n_cols, 6)).to(DEV)
+    h1, keep1 = _handle(L, 32, 1, 1)
+    h2, keep2 = _handle(L, 32, 1, 2)
+    try:
+        assert oracle.structure(L.rowPointers, 32, 1, 1)[1][:, 3].max() > 64
+        assert _status(lambda: api.argcsr_probe_gather(h1, xl.data_ptr(), 1)) == api.ARGCSR_ENOTSUP
+        assert _status(lambda: api.argcsr_probe_gather(h2, xl.data_ptr(), 1)) == api.ARGCSR_OK
+        torch.cuda.synchronize()
+    finally:
+        api.argcsr_destroy(h1)
+        api.argcsr_destroy(h2)
+
+
+def test_probe_rejects_malformed_modes():
+    A = synth.random_csr(5000, 4000, 34, mean_len=6.0)
+    h, keep = _handle(A, 32, 8, 1)
+    x = torch.from_numpy(synth.uniform_vector(A.n_cols, 7)).to(DEV)
+    try:
+        for mode in (3, 7, 11, 15, 16, -1):
+            assert _status(lambda: api.argcsr_probe_gather(h, x.data_ptr(), mode)) == api.ARGCSR_EINVAL
+        # no x where the mode gathers
+        assert _status(lambda: api.argcsr_probe_gather(h, 0, 0)) == api.ARGCSR_EINVAL
+        assert _status(lambda: api.argcsr_probe_gather(h, 0, 2)) == api.ARGCSR_OK
+        torch.cuda.synchronize()
+    finally:
+        api.argcsr_destroy(h)

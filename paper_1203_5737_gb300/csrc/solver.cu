@@ -357,6 +357,11 @@ public:
         if (e == cudaSuccess) e = cudaMemsetAsync(S_, 0, sizeof(CgState), s_);
         if (e != cudaSuccess) return fail(record_cuda(e, "cg job start"));
         inner_tol_ = P_.inner_tol > 0 ? P_.inner_tol : (sizeof(WT) == 4 ? 1e-5 : P_.tol);
+        // the inner iteration's vector kernels get at most one wave of
+        // resident blocks each (their loops stride over the rest)
+        alphaBlocks_ = resident_grid(k_cg_alpha<WT>);
+        updateBlocks_ = resident_grid(k_cg_update<WT>);
+        directionBlocks_ = resident_grid(k_cg_direction<WT>);
         check_ = P_.check_every > 0 ? P_.check_every : 16;
         // Graph replay needs a stream that can be captured (not the legacy
         // default stream, not synchronising with it) and no kernel tracing
@@ -487,15 +492,15 @@ private:
             if (st != ARGCSR_OK) return st;
             {
                 TraceScope t("k_cg_alpha", s_);
-                k_cg_alpha<WT><<<blocks_, kVecThreads, 0, s_>>>(p_, q_, n_, partials_, S_);
+                k_cg_alpha<WT><<<alphaBlocks_, kVecThreads, 0, s_>>>(p_, q_, n_, partials_, S_);
             }
             {
                 TraceScope t("k_cg_update", s_);
-                k_cg_update<WT><<<blocks_, kVecThreads, 0, s_>>>(d_, r_, p_, q_, n_, partials_, S_);
+                k_cg_update<WT><<<updateBlocks_, kVecThreads, 0, s_>>>(d_, r_, p_, q_, n_, partials_, S_);
             }
             {
                 TraceScope t("k_cg_direction", s_);
-                k_cg_direction<WT><<<blocks_, kVecThreads, 0, s_>>>(p_, r_, n_, S_);
+                k_cg_direction<WT><<<directionBlocks_, kVecThreads, 0, s_>>>(p_, r_, n_, S_);
             }
             count_launches(3);
         }
@@ -516,6 +521,20 @@ private:
     argcsr_cg_params P_;
     cudaStream_t s_;
     int blocks_;
+    int alphaBlocks_ = 1, updateBlocks_ = 1, directionBlocks_ = 1;
+
+    // blocks_, or fewer: as many blocks of `kernel` as the GPU holds at once
+    template <typename K>
+    int resident_grid(K kernel) const {
+        int dev = 0, sms = 0, per_sm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kVecThreads, 0) != cudaSuccess ||
+            per_sm < 1)
+            return blocks_;
+        const long long cap = (long long)per_sm * sms;
+        return (int)(blocks_ < cap ? blocks_ : cap);
+    }
     WT *r_ = nullptr, *p_ = nullptr, *q_ = nullptr, *d_ = nullptr;
     double *r64_ = nullptr, *partials_ = nullptr;
     CgState *S_ = nullptr, *hS_ = nullptr;

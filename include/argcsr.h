@@ -489,7 +489,9 @@ ARGCSR_API argcsr_status argcsr_server_destroy(argcsr_server_t server);
  *                    chunkSize} per group, 16-byte aligned),
  *   d_threadsMapping int32[n_rows] (always written),
  *   d_out_columns    int32[slot_capacity],
- *   d_out_values     slot_capacity elements of `dtype`.
+ *   d_out_values     slot_capacity elements of `dtype`;
+ *   with vec_width above 1 both are written V elements at a time and must
+ *   be 16-byte aligned (ARGCSR_EINVAL otherwise).
  * *h_n_groups and *h_n_slots receive the required sizes.  If a capacity is
  * too small the call returns ARGCSR_EINVAL after setting them, writes no
  * group records or slots, and can be repeated with larger buffers (pass 0

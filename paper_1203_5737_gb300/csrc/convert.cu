@@ -547,6 +547,34 @@ __device__ __forceinline__ VO to_storage(VI v) {
     }
 }
 
+// V consecutive elements stored with one vector store (the address is a
+// multiple of V elements).
+template <int V, typename T>
+__device__ __forceinline__ void store_vec(T *__restrict__ p, const T (&v)[V]) {
+    constexpr int B = V * (int)sizeof(T);
+    if constexpr (V == 1) {
+        *p = v[0];
+    } else if constexpr (B == 4) {
+        unsigned u;
+        memcpy(&u, v, 4);
+        *reinterpret_cast<unsigned *>(p) = u;
+    } else if constexpr (B == 8) {
+        uint2 u;
+        memcpy(&u, v, 8);
+        *reinterpret_cast<uint2 *>(p) = u;
+    } else if constexpr (B == 16) {
+        uint4 u;
+        memcpy(&u, v, 16);
+        *reinterpret_cast<uint4 *>(p) = u;
+    } else {
+        static_assert(B == 32, "unsupported vector store");
+        uint4 u[2];
+        memcpy(u, v, 32);
+        reinterpret_cast<uint4 *>(p)[0] = u[0];
+        reinterpret_cast<uint4 *>(p)[1] = u[1];
+    }
+}
+
 // One chunk of a group: C elements from src (fill of them real, the rest
 // padding) to slots out[(j / V) G V + j % V], j < C.
 template <int G, int V, typename VT, typename VO>
@@ -567,13 +595,19 @@ __device__ __forceinline__ void copy_chunk(const int *__restrict__ cIn, const VT
                 bad |= (cc[u] < 0) | (cc[u] >= n_cols);
             }
         }
+        // the V slots of one slot-row step sit side by side: one store each
+        // (C is a multiple of V, so a step is all in or all out)
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 4; u += V) {
             const int j = j0 + u;
             if (j < C) {
-                const int at = (j / V) * (G * V) + (j % V);
-                cOut[at] = cc[u];
-                vOut[at] = to_storage<VO>(vv[u]);
+                int oc[V];
+                VO ov[V];
+#pragma unroll
+                for (int k = 0; k < V; ++k) { oc[k] = cc[u + k]; ov[k] = to_storage<VO>(vv[u + k]); }
+                const int at = (j / V) * (G * V);
+                store_vec<V>(cOut + at, oc);
+                store_vec<V>(vOut + at, ov);
             }
         }
     }
@@ -1076,6 +1110,9 @@ extern "C" ARGCSR_API argcsr_status argcsr_convert_noalloc(
         return fail(ARGCSR_EINVAL, "argcsr_convert_noalloc: null threadsMapping or negative capacity");
     if (reinterpret_cast<uintptr_t>(d_groupInfo) % 16)   // int4 records
         return fail(ARGCSR_EINVAL, "argcsr_convert_noalloc: d_groupInfo is not 16-byte aligned");
+    // k_fill stores the V slots of a slot-row step with one vector store
+    if (V > 1 && (reinterpret_cast<uintptr_t>(d_out_columns) % 16 || reinterpret_cast<uintptr_t>(d_out_values) % 16))
+        return fail(ARGCSR_EINVAL, "argcsr_convert_noalloc: with vec_width above 1 the output arrays must be 16-byte aligned");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
 
     unsigned char *base = nullptr;

@@ -233,3 +233,32 @@ def test_first_call_in_a_fresh_process():
                        text=True, timeout=600)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "first call ok" in r.stdout
+
+
+def test_vector_outputs_must_be_16_byte_aligned():
+    """With vec_width above 1 the slots are stored V at a time: output arrays
+    off a 16-byte boundary are refused before any kernel runs."""
+    A = synth.random_csr(3000, 2000, 41, mean_len=6)
+    rp, cols, vals = _device_csr(A)
+    ref = oracle.convert(A, 32, 4, 2)
+    s = torch.cuda.current_stream().cuda_stream
+    tm = torch.empty(A.n_rows, dtype=torch.int32, device=DEV)
+    gi = torch.empty((ref.n_groups, 4), dtype=torch.int32, device=DEV)
+    oc = torch.empty(ref.n_slots + 4, dtype=torch.int32, device=DEV)
+    ov = torch.empty(ref.n_slots + 2, dtype=torch.float64, device=DEV)
+    for c_off, v_off in ((4, 0), (0, 8)):
+        st, _, _ = api.argcsr_convert_noalloc(A.n_rows, A.n_cols, A.nnz, rp.data_ptr(), cols.data_ptr(),
+                                              vals.data_ptr(), api.ARGCSR_F64, 32, 4, 2, gi.data_ptr(),
+                                              ref.n_groups, tm.data_ptr(), oc.data_ptr() + c_off,
+                                              ov.data_ptr() + v_off, ref.n_slots, s)
+        assert st == api.ARGCSR_EINVAL
+        assert "16-byte aligned" in api.argcsr_last_error_message()
+    # aligned: the oracle's arrays
+    st, ng, ns = api.argcsr_convert_noalloc(A.n_rows, A.n_cols, A.nnz, rp.data_ptr(), cols.data_ptr(),
+                                            vals.data_ptr(), api.ARGCSR_F64, 32, 4, 2, gi.data_ptr(),
+                                            ref.n_groups, tm.data_ptr(), oc.data_ptr(), ov.data_ptr(),
+                                            ref.n_slots, s)
+    torch.cuda.synchronize()
+    assert st == api.ARGCSR_OK
+    assert np.array_equal(oc[:ns].cpu().numpy(), ref.columns)
+    assert np.array_equal(ov[:ns].cpu().numpy(), ref.values)

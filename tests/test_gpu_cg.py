@@ -65,7 +65,10 @@ def check_solution(A, x, x_true, b, cond, tol=TOL):
 
 
 @pytest.mark.parametrize("storage", ["f64", "f32", "bf16"])
-@pytest.mark.parametrize("dims,G,D", [((24, 20, 16), 32, 8), ((64, 64), 128, 4)])
+# n = 7680 and 4096, and n % 4 = 1, 3 and n = 3 (the FP32 vector kernels take
+# 16-byte pieces of 4 floats and finish the rest element by element)
+@pytest.mark.parametrize("dims,G,D", [((24, 20, 16), 32, 8), ((64, 64), 128, 4), ((23, 19, 17), 32, 8),
+                                      ((65, 63), 64, 4), ((3, 1), 32, 8)])
 def test_poisson_ir(storage, dims, G, D):
     A = synth.laplacian_3d(dims[2], dims[1], dims[0]) if len(dims) == 3 else synth.laplacian_2d(dims[1], dims[0])
     x_true, b = problem(A)

@@ -231,12 +231,6 @@ ARGCSR_API argcsr_status argcsr_probe_gather(argcsr_t A, const void *d_x, int32_
         set_error_message("argcsr_probe_gather: only G = 32, V = 1 or 2, f64 handles");
         return ARGCSR_ENOTSUP;
     }
-    if (A->V == 1 && A->n_long > 0) {
-        // the product runs these groups on whole blocks; the probe keeps one
-        // warp per group, so its accesses would not be the product's
-        set_error_message("argcsr_probe_gather: V = 1 handles with groups of chunk size above 64");
-        return ARGCSR_ENOTSUP;
-    }
     if (A->n_rows == 0) return ARGCSR_OK;
     if (!d_x && A->n_cols > 0 && (mode & 3) != 2) return ARGCSR_EINVAL;
     return launch_probe_gather(A, d_x, mode, reinterpret_cast<cudaStream_t>(stream));

@@ -488,16 +488,30 @@ __device__ unsigned long long g_probe_sink;
 template <int MODE, int OP, int V>
 __global__ void __launch_bounds__(256, 8)
 k_probe_g32(long long nGroups, const int4 *__restrict__ gi, const int *__restrict__ cols,
-            const double *__restrict__ vals, const double *__restrict__ x) {
+            const double *__restrict__ vals, const double *__restrict__ x, const int *__restrict__ longList,
+            int nLong) {
     constexpr int U = (ARGCSR_SPMV_ELEMS + V - 1) / V;   // V-blocks per batch
-    const int lane = threadIdx.x & 31;
-    const long long g = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (g >= nGroups) return;   // warp-uniform
-    const int4 info = __ldg(gi + g);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // the product's split of the work: the long groups (V = 1) first, one per
+    // block with its slot rows shared out among the 8 warps, then one group
+    // per warp
+    int4 info;
+    int j0, nb;
+    if (V == 1 && (int)blockIdx.x < nLong) {   // block-uniform
+        info = __ldg(gi + __ldg(longList + blockIdx.x));
+        j0 = (int)((long long)info.w * warp / 8);
+        nb = (int)((long long)info.w * (warp + 1) / 8);
+    } else {
+        const long long g = (long long)(blockIdx.x - nLong) * 8 + warp;
+        if (g >= nGroups) return;   // warp-uniform
+        info = __ldg(gi + g);
+        if (nLong > 0 && info.w > kLongChunk) return;   // done by one of the first blocks
+        j0 = 0;
+        nb = info.w / V;
+    }
     const long long base = (long long)info.z + lane * V;
-    const int nb = info.w / V;
     unsigned long long acc = 0;
-    for (int j = 0; j < nb; j += U) {
+    for (int j = j0; j < nb; j += U) {
         int c[U][V];
         double v[U][V];
 #pragma unroll
@@ -525,13 +539,18 @@ k_probe_g32(long long nGroups, const int4 *__restrict__ gi, const int *__restric
 }
 
 template <int MODE, int V>
-void launch_probe_mode(unsigned blocks, const argcsr_matrix *A, const double *x, int op, cudaStream_t s) {
+void launch_probe_mode(unsigned blocks, const argcsr_matrix *A, const double *x, int op, int nLong,
+                       cudaStream_t s) {
     const auto *v = static_cast<const double *>(A->d_values);
     switch (op) {
-        case 0: k_probe_g32<MODE, 0, V><<<blocks, 256, 0, s>>>(A->n_groups, A->d_groupInfo, A->d_columns, v, x); break;
-        case 1: k_probe_g32<MODE, 1, V><<<blocks, 256, 0, s>>>(A->n_groups, A->d_groupInfo, A->d_columns, v, x); break;
-        case 2: k_probe_g32<MODE, 2, V><<<blocks, 256, 0, s>>>(A->n_groups, A->d_groupInfo, A->d_columns, v, x); break;
-        default: k_probe_g32<MODE, 3, V><<<blocks, 256, 0, s>>>(A->n_groups, A->d_groupInfo, A->d_columns, v, x); break;
+        case 0: k_probe_g32<MODE, 0, V><<<blocks, 256, 0, s>>>(A->n_groups, A->d_groupInfo, A->d_columns, v, x,
+                                                                    A->d_longGroups, nLong); break;
+        case 1: k_probe_g32<MODE, 1, V><<<blocks, 256, 0, s>>>(A->n_groups, A->d_groupInfo, A->d_columns, v, x,
+                                                                    A->d_longGroups, nLong); break;
+        case 2: k_probe_g32<MODE, 2, V><<<blocks, 256, 0, s>>>(A->n_groups, A->d_groupInfo, A->d_columns, v, x,
+                                                                    A->d_longGroups, nLong); break;
+        default: k_probe_g32<MODE, 3, V><<<blocks, 256, 0, s>>>(A->n_groups, A->d_groupInfo, A->d_columns, v, x,
+                                                                    A->d_longGroups, nLong); break;
     }
 }
 
@@ -539,18 +558,19 @@ void launch_probe_mode(unsigned blocks, const argcsr_matrix *A, const double *x,
 
 argcsr_status launch_probe_gather(const argcsr_matrix *A, const void *x, int mode, cudaStream_t s) {
     if (A->n_groups == 0) return ARGCSR_OK;
-    const unsigned blocks = (unsigned)((A->n_groups + 7) / 8);
+    const int nLong = A->V == 1 ? (int)A->n_long : 0;
+    const unsigned blocks = (unsigned)((A->n_groups + 7) / 8 + nLong);
     const int what = mode & 3, op = (mode >> 2) & 3;
     const double *xx = static_cast<const double *>(x);
     TraceScope t("k_probe_g32", s);
     if (A->V == 2) {
-        if (what == 0) launch_probe_mode<0, 2>(blocks, A, xx, op, s);
-        else if (what == 1) launch_probe_mode<1, 2>(blocks, A, xx, op, s);
-        else launch_probe_mode<2, 2>(blocks, A, xx, op, s);
+        if (what == 0) launch_probe_mode<0, 2>(blocks, A, xx, op, nLong, s);
+        else if (what == 1) launch_probe_mode<1, 2>(blocks, A, xx, op, nLong, s);
+        else launch_probe_mode<2, 2>(blocks, A, xx, op, nLong, s);
     } else {
-        if (what == 0) launch_probe_mode<0, 1>(blocks, A, xx, op, s);
-        else if (what == 1) launch_probe_mode<1, 1>(blocks, A, xx, op, s);
-        else launch_probe_mode<2, 1>(blocks, A, xx, op, s);
+        if (what == 0) launch_probe_mode<0, 1>(blocks, A, xx, op, nLong, s);
+        else if (what == 1) launch_probe_mode<1, 1>(blocks, A, xx, op, nLong, s);
+        else launch_probe_mode<2, 1>(blocks, A, xx, op, nLong, s);
     }
     count_launches(1);
     ARGCSR_CHECK_LAUNCH("k_probe_g32");

@@ -1,8 +1,8 @@
 """argcsr_probe_gather: the product's memory accesses without its arithmetic,
 the roofline probe the bench reports its gather and access ceilings from.
-It runs on the layouts it models (G = 32, FP64, V 1 or 2), writes no caller
-memory, leaves the device usable, and refuses the layouts it does not model
-and malformed modes."""
+It runs on the layouts it models (G = 32, FP64, V 1 or 2, long groups split
+as the product splits them), writes no caller memory, leaves the device
+usable, and refuses the other layouts and malformed modes."""
 import numpy as np
 import pytest
 
@@ -80,20 +80,30 @@ def test_probe_refuses_layouts_it_does_not_model():
             assert _status(lambda: api.argcsr_probe_gather(h, x.data_ptr(), 0)) == api.ARGCSR_ENOTSUP
         finally:
             api.argcsr_destroy(h)
-    # long groups (chunk size above 64): V = 1 gives them whole blocks in the
-    # product, which the probe does not do; V = 2 keeps a warp per group
+
+
+@pytest.mark.parametrize("V", [1, 2])
+def test_probe_runs_on_long_groups(V):
+    """Groups of chunk size above 64: with V = 1 the product gives each a
+    whole block, and the probe splits them the same way."""
     L = synth.random_csr(20000, 15000, 33, mean_len=8.0, n_huge=4, huge_len=6000)
+    assert oracle.structure(L.rowPointers, 32, 1, V)[1][:, 3].max() > 64
     xl = torch.from_numpy(synth.uniform_vector(L.n_cols, 6)).to(DEV)
-    h1, keep1 = _handle(L, 32, 1, 1)
-    h2, keep2 = _handle(L, 32, 1, 2)
+    x0 = xl.clone()
+    h, keep = _handle(L, 32, 1, V)
     try:
-        assert oracle.structure(L.rowPointers, 32, 1, 1)[1][:, 3].max() > 64
-        assert _status(lambda: api.argcsr_probe_gather(h1, xl.data_ptr(), 1)) == api.ARGCSR_ENOTSUP
-        assert _status(lambda: api.argcsr_probe_gather(h2, xl.data_ptr(), 1)) == api.ARGCSR_OK
+        for what in (0, 1, 2):
+            api.argcsr_probe_gather(h, xl.data_ptr(), what)
         torch.cuda.synchronize()
+        assert torch.equal(xl, x0)
+        y = torch.empty(L.n_rows, dtype=torch.float64, device=DEV)
+        api.argcsr_spmv(h, xl.data_ptr(), y.data_ptr())
+        torch.cuda.synchronize()
+        xh = xl.cpu().numpy()
+        ref, scale = oracle.csr_spmv(L, xh), oracle.csr_abs_spmv(L, xh)
+        assert (np.abs(y.cpu().numpy() - ref) / np.maximum(scale, 1e-300)).max() <= 1e-13
     finally:
-        api.argcsr_destroy(h1)
-        api.argcsr_destroy(h2)
+        api.argcsr_destroy(h)
 
 
 def test_probe_rejects_malformed_modes():

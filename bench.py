@@ -615,15 +615,14 @@ def run_ours(args):
             info = api.argcsr_info(h)
             nb = spmv_bytes(A.n_rows, A.n_cols, A.nnz, info.n_groups)
             us = _time_us(torch, stream, lambda: api.argcsr_spmv(h, x.data_ptr(), y.data_ptr(), s), 20, 3)
-            # the ceilings of the layout's memory accesses (the probe covers
-            # G 32, V <= 2): mode 0 columns + x gathers, 1 with the values
+            # the ceilings of the layout's memory accesses: mode 0 columns +
+            # x gathers, 1 with the values
             ceil, no_ceil = {}, None
-            if G == 32 and V <= 2:
-                try:
-                    ceil = {md: round(_time_us(torch, stream, lambda: api.argcsr_probe_gather(
-                        h, x.data_ptr(), md, s), 20, 3), 2) for md in (0, 1)}
-                except api.ArgcsrError as e:   # layouts the probe does not model
-                    no_ceil = str(e)
+            try:
+                ceil = {md: round(_time_us(torch, stream, lambda: api.argcsr_probe_gather(
+                    h, x.data_ptr(), md, s), 20, 3), 2) for md in (0, 1)}
+            except api.ArgcsrError as e:   # layouts the probe does not model
+                no_ceil = str(e)
             api.argcsr_destroy(h, s)
             cb = csr_spmv_bytes(A.n_rows, A.n_cols, A.nnz)
             vec = _time_us(torch, stream, lambda: api.argcsr_baseline_csr_spmv(

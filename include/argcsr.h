@@ -185,9 +185,11 @@ ARGCSR_API argcsr_status argcsr_spmv_axpby(argcsr_t A, double alpha, const void 
  *   (mode >> 2) & 3: the gather's load instruction: 0 read-only path,
  *                    1 read-only without L1 allocation, 2 L2 only,
  *                    3 default caching load
- * The work is split as the product splits it (for V = 1, groups of chunk
- * size above 64 get a whole block each).  Only G = 32, ARGCSR_F64 handles
- * with V in {1, 2} (ARGCSR_ENOTSUP otherwise);
+ * The work is split as the product splits it (G = 32: a warp per group,
+ * and for V = 1 groups of chunk size above 64 get a whole block each;
+ * G = 64 or 128: G threads per group).  ARGCSR_F64 handles only, and the
+ * load instruction choice (mode >> 2) only for G = 32 (ARGCSR_ENOTSUP
+ * otherwise);
  * other modes return ARGCSR_EINVAL.  d_x as in argcsr_spmv.  Writes no
  * caller memory.  Asynchronous on `stream`; one kernel.
  * ------------------------------------------------------------------------ */

@@ -227,8 +227,8 @@ ARGCSR_API argcsr_status argcsr_spmv(argcsr_t A, const void *d_x, void *d_y, arg
 ARGCSR_API argcsr_status argcsr_probe_gather(argcsr_t A, const void *d_x, int32_t mode,
                                              argcsr_stream_t stream) {
     if (!A || mode < 0 || (mode & 3) == 3 || mode > 15) return ARGCSR_EINVAL;
-    if (A->G != 32 || A->V > 2 || A->dtype != ARGCSR_F64) {
-        set_error_message("argcsr_probe_gather: only G = 32, V = 1 or 2, f64 handles");
+    if (A->dtype != ARGCSR_F64 || (A->G != 32 && (mode >> 2) != 0)) {
+        set_error_message("argcsr_probe_gather: f64 handles only; load instruction choices for G = 32 only");
         return ARGCSR_ENOTSUP;
     }
     if (A->n_rows == 0) return ARGCSR_OK;

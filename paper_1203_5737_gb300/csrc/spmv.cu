@@ -538,6 +538,63 @@ k_probe_g32(long long nGroups, const int4 *__restrict__ gi, const int *__restric
     if (acc == 0x5a5a5a5a5a5a5a5aULL) g_probe_sink = acc;
 }
 
+// The probe for G = 64 or 128 layouts, in k_spmv_block's split: one group
+// per G threads, thread c reading chunk c (V-blocks G V apart).
+template <int G, int MODE, int V>
+__global__ void __launch_bounds__(256)
+k_probe_block(long long nGroups, const int4 *__restrict__ gi, const int *__restrict__ cols,
+              const double *__restrict__ vals, const double *__restrict__ x) {
+    constexpr int U = (ARGCSR_SPMV_ELEMS + V - 1) / V;
+    const int sub = threadIdx.x / G, c = threadIdx.x % G;
+    const long long g = (long long)blockIdx.x * (256 / G) + sub;
+    if (g >= nGroups) return;   // uniform over the group's G threads (whole warps)
+    const int4 info = __ldg(gi + g);
+    const long long base = (long long)info.z + c * V;
+    const int nb = info.w / V;
+    unsigned long long acc = 0;
+    for (int j = 0; j < nb; j += U) {
+        int cc[U][V];
+        double v[U][V];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+#pragma unroll
+            for (int e = 0; e < V; ++e) { cc[u][e] = -1; v[u][e] = 0.0; }
+            if (j + u < nb) {
+                ld_stream<int, V>(cols + base + (long long)G * V * (j + u), cc[u]);
+                if constexpr (MODE == 1) ld_stream<double, V>(vals + base + (long long)G * V * (j + u), v[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                if constexpr (MODE == 2) {
+                    acc ^= (unsigned)cc[u][e];
+                } else if (cc[u][e] >= 0) {
+                    acc ^= (unsigned long long)__double_as_longlong(ldx<0>(x + cc[u][e]));
+                    if constexpr (MODE == 1) acc ^= (unsigned long long)__double_as_longlong(v[u][e]);
+                }
+            }
+    }
+    if (acc == 0x5a5a5a5a5a5a5a5aULL) g_probe_sink = acc;
+}
+
+template <int G, int V>
+void launch_probe_block(const argcsr_matrix *A, const double *x, int what, cudaStream_t s) {
+    const unsigned blocks = (unsigned)((A->n_groups + 256 / G - 1) / (256 / G));
+    const auto *v = static_cast<const double *>(A->d_values);
+    if (what == 0) k_probe_block<G, 0, V><<<blocks, 256, 0, s>>>(A->n_groups, A->d_groupInfo, A->d_columns, v, x);
+    else if (what == 1) k_probe_block<G, 1, V><<<blocks, 256, 0, s>>>(A->n_groups, A->d_groupInfo, A->d_columns, v, x);
+    else k_probe_block<G, 2, V><<<blocks, 256, 0, s>>>(A->n_groups, A->d_groupInfo, A->d_columns, v, x);
+}
+
+template <int G>
+void launch_probe_block_v(const argcsr_matrix *A, const double *x, int what, cudaStream_t s) {
+    if (A->V == 1) launch_probe_block<G, 1>(A, x, what, s);
+    else if (A->V == 2) launch_probe_block<G, 2>(A, x, what, s);
+    else launch_probe_block<G, 4>(A, x, what, s);
+}
+
 template <int MODE, int V>
 void launch_probe_mode(unsigned blocks, const argcsr_matrix *A, const double *x, int op, int nLong,
                        cudaStream_t s) {
@@ -562,8 +619,20 @@ argcsr_status launch_probe_gather(const argcsr_matrix *A, const void *x, int mod
     const unsigned blocks = (unsigned)((A->n_groups + 7) / 8 + nLong);
     const int what = mode & 3, op = (mode >> 2) & 3;
     const double *xx = static_cast<const double *>(x);
+    if (A->G != 32) {
+        TraceScope t("k_probe_block", s);
+        if (A->G == 64) launch_probe_block_v<64>(A, xx, what, s);
+        else launch_probe_block_v<128>(A, xx, what, s);
+        count_launches(1);
+        ARGCSR_CHECK_LAUNCH("k_probe_block");
+        return ARGCSR_OK;
+    }
     TraceScope t("k_probe_g32", s);
-    if (A->V == 2) {
+    if (A->V == 4) {
+        if (what == 0) launch_probe_mode<0, 4>(blocks, A, xx, op, nLong, s);
+        else if (what == 1) launch_probe_mode<1, 4>(blocks, A, xx, op, nLong, s);
+        else launch_probe_mode<2, 4>(blocks, A, xx, op, nLong, s);
+    } else if (A->V == 2) {
         if (what == 0) launch_probe_mode<0, 2>(blocks, A, xx, op, nLong, s);
         else if (what == 1) launch_probe_mode<1, 2>(blocks, A, xx, op, nLong, s);
         else launch_probe_mode<2, 2>(blocks, A, xx, op, nLong, s);

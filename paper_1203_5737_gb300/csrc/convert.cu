@@ -199,6 +199,7 @@ template <int G>
 __global__ void __launch_bounds__(1024)
 k_resolve(int numTiles, const uint8_t *__restrict__ fn, const int *__restrict__ cnt,
           int *__restrict__ tileEntry, int *__restrict__ tileGroupBase, DeviceTotals *tot) {
+    pdl_trigger();   // k_groups may start its per-tile work that needs no entry
     constexpr int E = G / 32;
     __shared__ int segF[32][G];
     __shared__ int segC[32][G];
@@ -317,6 +318,9 @@ k_groups(int n, int T, int V, int onePerRow, int gallop, const int *__restrict__
     // per sub-tile tables, one pass over the S sub-tiles, per sub-tile walks
     subtile_tables<G>(d, lim, B, S, fnA, cntA);
     __syncthreads();
+    // everything above reads only rowPointers and k_tile_prepare's deltas;
+    // the tile's entry and first group index come from k_resolve
+    pdl_wait();
     if (threadIdx.x == 0) {
         int entry = tileEntry[k], base = 0;
         for (int sub = 0; sub < S; ++sub) {
@@ -673,6 +677,7 @@ k_fill(long long nGroups, int n_cols, const long long *__restrict__ tileSlotBase
     if constexpr (G == 32) {
         fill_g32<VT, VO, V>(nGroups, n_cols, tileSlotBase, gscratch, rp, colsIn, valsIn, threadsMapping,
                             groupInfo, colsOut, valsOut, tot);
+        pdl_wait();   // this kernel ends after k_order, which runs alongside it
     } else {
         // G = 64 or 128: one group per warp; the row of each chunk from a
         // per-warp table built from threadsMapping
@@ -713,6 +718,7 @@ k_fill(long long nGroups, int n_cols, const long long *__restrict__ tileSlotBase
             __syncwarp();
         }
         if (__any_sync(FULL, bad) && lane == 0) flag(&tot->status, kBadColumn);
+        pdl_wait();   // this kernel ends after k_order, which runs alongside it
     }
 }
 
@@ -726,6 +732,7 @@ __global__ void __launch_bounds__(256)
 k_order(long long nGroups, const long long *__restrict__ tileSlotBase, const int4 *__restrict__ gscratch,
         int4 *__restrict__ groupInfo, int *__restrict__ orderCursor, int *__restrict__ longList,
         long long longCap, DeviceTotals *tot) {
+    pdl_trigger();   // k_fill reads nothing this kernel writes: it may run alongside
     // positions are handed out per block: ranks inside the block from
     // shared-memory counters, then one global reservation per bucket the
     // block uses
@@ -790,8 +797,13 @@ struct Kernels {
         {
             TraceScope t("k_groups", s);
             const size_t smem = groups_smem(T, G);
-            k_groups<G><<<numTiles, kTileThreads, smem, s>>>(n, T, V, onePerRow, limit <= 6LL * G ? 1 : 0, rp, delta, tileEntry, tileGroupBase,
-                                                     gscratch, tm, tileSlots, hist, tot);
+            // launched behind k_resolve's start: the per-tile work that needs
+            // no tile entry overlaps k_resolve's single block
+            const cudaError_t e = launch_pdl(k_groups<G>, (unsigned)numTiles, kTileThreads, smem, s, n, T, V, onePerRow,
+                                             limit <= 6LL * G ? 1 : 0, rp, (const uint8_t *)delta,
+                                             (const int *)tileEntry, (const int *)tileGroupBase, gscratch, tm,
+                                             tileSlots, hist, tot);
+            if (e != cudaSuccess) return record_cuda(e, "k_groups launch");
         }
         {
             TraceScope t("k_tile_scan", s);
@@ -819,15 +831,22 @@ struct Kernels {
         TraceScope t("k_fill", s);
         const VT *v = static_cast<const VT *>(vals);
         VO *vo = static_cast<VO *>(valsOut);
+        // launched behind k_order's start (programmatic serialization): the
+        // two share no data, and k_fill's last act waits for k_order
+        cudaError_t e;
         if (V == 1)
-            k_fill<G, VT, VO, 1><<<(unsigned)blocks, 256, 0, s>>>(nGroups, n_cols, tileSlotBase, gscratch, rp,
-                                                                  cols, v, tm, gi, colsOut, vo, tot);
+            e = launch_pdl(k_fill<G, VT, VO, 1>, (unsigned)blocks, 256, 0, s, nGroups, n_cols,
+                           (const long long *)tileSlotBase, (const int4 *)gscratch, rp, cols, v, tm, gi, colsOut,
+                           vo, tot);
         else if (V == 2)
-            k_fill<G, VT, VO, 2><<<(unsigned)blocks, 256, 0, s>>>(nGroups, n_cols, tileSlotBase, gscratch, rp,
-                                                                  cols, v, tm, gi, colsOut, vo, tot);
+            e = launch_pdl(k_fill<G, VT, VO, 2>, (unsigned)blocks, 256, 0, s, nGroups, n_cols,
+                           (const long long *)tileSlotBase, (const int4 *)gscratch, rp, cols, v, tm, gi, colsOut,
+                           vo, tot);
         else
-            k_fill<G, VT, VO, 4><<<(unsigned)blocks, 256, 0, s>>>(nGroups, n_cols, tileSlotBase, gscratch, rp,
-                                                                  cols, v, tm, gi, colsOut, vo, tot);
+            e = launch_pdl(k_fill<G, VT, VO, 4>, (unsigned)blocks, 256, 0, s, nGroups, n_cols,
+                           (const long long *)tileSlotBase, (const int4 *)gscratch, rp, cols, v, tm, gi, colsOut,
+                           vo, tot);
+        if (e != cudaSuccess) return record_cuda(e, "k_fill launch");
         count_launches(1);
         ARGCSR_CHECK_LAUNCH("k_fill");
         return ARGCSR_OK;

@@ -18,6 +18,31 @@ enum : unsigned {
     kSlotOverflow   = 4u,  // more than 2^31 - 1 slots
 };
 
+// Programmatic dependent launch.  A kernel launched with the programmatic
+// stream serialization attribute (launch_pdl) may start while the kernel
+// ahead of it on the stream is still running; pdl_wait() returns once that
+// kernel has completed and its writes are visible, so nothing it writes may
+// be touched before the call.  pdl_trigger() lets the next such kernel
+// launch.  For kernels launched without the attribute both return at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr = {};
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Totals produced on the device during conversion and read back once.
 struct DeviceTotals {
     unsigned status;

@@ -23,10 +23,10 @@
 //      inclusive prefix (threadsMapping), and the group's slot offset inside
 //      the tile;
 //   5. k_tile_scan turns the per-tile slot totals into tile offsets;
-//   6. after one read-back of the totals, k_fill writes the group records,
-//      copies the CSR entries chunk by chunk into the interleaved arrays and
-//      lists the long groups for the product; a second read-back returns
-//      the column check.
+//   6. after one read-back of the totals, k_order writes the group records
+//      in execution order and lists the long groups for the product, while
+//      k_fill copies the CSR entries chunk by chunk into the interleaved
+//      arrays; a second read-back returns the column check.
 //
 // Chunk size (Section 3, step 2).  The greedy -- repeatedly hand one more
 // thread to the row whose chunks are fullest, until the G threads are used

@@ -44,7 +44,7 @@ typedef enum {
     ARGCSR_ENOMEM    = -2,  /* device allocation failed                   */
     ARGCSR_ECUDA     = -3,  /* a CUDA runtime call or launch failed       */
     ARGCSR_EOVERFLOW = -4,  /* more than 2^31 - 1 slots would be needed   */
-    ARGCSR_ENOTSUP   = -5   /* valid request this build does not support  */
+    ARGCSR_ENOTSUP   = -5   /* valid request the library does not support */
 } argcsr_status;
 
 /* Element type of the stored values and of x and y. */

@@ -170,3 +170,21 @@ def test_digest_ignores_comments():
     assert bench.strip_comments(code) == bench.strip_comments(
         "/* a block\n comment */\n" + code.replace("// add one", "// another note") + "\n\n")
     assert bench.strip_comments(code) != bench.strip_comments(code.replace("+ 1", "+ 2"))
+
+
+def test_serving_runs_repeat_until_on_schedule():
+    lags = iter([40.0, 2.0, 1.0])
+    calls = []
+
+    def run():
+        calls.append(1)
+        return {"client_max_lag_ms": next(lags), "p99_ms": 1.0}
+    r = bench._on_schedule(run)
+    assert len(calls) == 2 and r["client_max_lag_ms"] == 2.0 and r["tries"] == 2
+    # never on schedule: three tries, the least lag kept
+    lags = iter([40.0, 9.0, 30.0])
+    r = bench._on_schedule(lambda: {"client_max_lag_ms": next(lags)})
+    assert r["tries"] == 3 and r["client_max_lag_ms"] == 9.0
+    # on schedule at once
+    r = bench._on_schedule(lambda: {"client_max_lag_ms": 0.1})
+    assert r["tries"] == 1

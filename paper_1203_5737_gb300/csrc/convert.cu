@@ -585,11 +585,14 @@ template <int G, int V, typename VT, typename VO>
 __device__ __forceinline__ void copy_chunk(const int *__restrict__ cIn, const VT *__restrict__ vIn, int fill,
                                            int C, int n_cols, int *__restrict__ cOut, VO *__restrict__ vOut,
                                            bool &bad) {
-    for (int j0 = 0; j0 < C; j0 += 4) {
-        int cc[4];
-        VT vv[4];
+    // elements per round: 8 for V >= 2 (fewer dependent load rounds per
+    // chunk), 4 for V = 1, where 8 was slower at D 4 and D 8
+    constexpr int R = V >= 2 ? 8 : 4;
+    for (int j0 = 0; j0 < C; j0 += R) {
+        int cc[R];
+        VT vv[R];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < R; ++u) {
             const int j = j0 + u;
             cc[u] = -1;
             memset(&vv[u], 0, sizeof(VT));
@@ -602,7 +605,7 @@ __device__ __forceinline__ void copy_chunk(const int *__restrict__ cIn, const VT
         // the V slots of one slot-row step sit side by side: one store each
         // (C is a multiple of V, so a step is all in or all out)
 #pragma unroll
-        for (int u = 0; u < 4; u += V) {
+        for (int u = 0; u < R; u += V) {
             const int j = j0 + u;
             if (j < C) {
                 int oc[V];

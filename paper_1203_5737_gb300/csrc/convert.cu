@@ -371,13 +371,41 @@ k_groups(int n, int T, int V, int onePerRow, int gallop, const int *__restrict__
             unsigned hi = maxlen;
             if (size < G) hi = min(hi, (unsigned)((nnz + (G - size) - 1) / (G - size)));
             lo = max(lo, 1u);
-            // threads needed with chunk size c (stops once above G)
+            // every trial size is at least lo, so only rows longer than lo
+            // can take more than one thread: when bisecting, list them once
+            // (a bit per row) and visit only those in each trial
+            constexpr int NW = G / 32;
+            unsigned longRows[NW];
+#pragma unroll
+            for (int q = 0; q < NW; ++q) {
+                unsigned bits = 0;
+                if (!gallop) {   // uniform over the launch
+                    const int r1 = min(size, 32 * (q + 1));
+                    for (int r = 32 * q; r < r1; ++r) bits |= ((unsigned)L(r) > lo ? 1u : 0u) << (r - 32 * q);
+                }
+                longRows[q] = bits;
+            }
+            // threads needed with chunk size c >= lo (stops once above G)
             auto need = [&](unsigned c) {
                 const unsigned m = 0xffffffffu / c;
                 int t = 0;
-                for (int r = 0; r < size && t <= G; ++r) {
-                    const unsigned l = (unsigned)L(r);
-                    t += l > c ? (int)ceil_div_by(l, c, m) : 1;
+                if (gallop) {
+                    for (int r = 0; r < size && t <= G; ++r) {
+                        const unsigned l = (unsigned)L(r);
+                        t += l > c ? (int)ceil_div_by(l, c, m) : 1;
+                    }
+                    return t;
+                }
+                t = size;   // one thread per row, plus the extra ones of long rows
+#pragma unroll
+                for (int q = 0; q < NW; ++q) {
+                    unsigned bits = longRows[q];
+                    while (bits && t <= G) {
+                        const int r = 32 * q + __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        const unsigned l = (unsigned)L(r);
+                        if (l > c) t += (int)ceil_div_by(l, c, m) - 1;
+                    }
                 }
                 return t;
             };
